@@ -1,0 +1,268 @@
+"""Benchmark: TEBD gate-updates/s at chi_max on one GB300 (and N replicas).
+
+Workload (default): L=32 Bose-Hubbard chain with NN+NNN hopping and a trap
+(U=5, J=1, J_NNN=0.12, K=0.005, j_c=16.5), d=4, chi_max=256, discarded-weight
+cut 1e-10, dt=0.01, started from the seeded synthetic saturated state
+(chi = min(256, 4^min(k, 32-k)) on every bond).  One step = one full
+second-order Trotter step (A/2 B/2 C B/2 A/2 = 50 three-site gate updates,
+100 truncated SVDs) plus the density/current measurement.  The state and
+the workspace (> 2 GB) exceed L2 (129 MB), so no flush is needed between steps.
+
+Multi-GPU: replicas only (independent simulations, one per rank, no
+collective on the data path); value = all ranks' gate updates / max time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (a few gate updates per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WL = workloads.TRUNC_L32
+GATES_PER_STEP = 50  # A(10) + B(10) + C(10) + B(10) + A(10) for L = 32
+METRIC = "TEBD gate-updates/s at chi_max"
+UNIT = "gate-updates/s"
+# FP64 on GB300: 152 SMs x 2 DFMA (4 flop) per clock x 2070 MHz (a DFMA throughput
+# probe measured 1.20 TFLOP/s at ~1970 MHz, i.e. 2 DFMA/clk/SM).
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+def config(precision: str):
+    return {"workload": f"L{WL.L}_d{WL.d}_chi{WL.chi_max}_wcut1e-10_synthetic_saturated",
+            "L": WL.L, "d": WL.d, "chi_max": WL.chi_max, "dt": WL.dt, "precision": precision,
+            "step": "one 2nd-order Trotter step (50 three-site gate updates) + n_j/current measurement",
+            "l2_flush": "not needed: state + workspace > 2 GB > 129 MB L2"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(n_gates: int, seed_state):
+    """Time the oracle on n_gates three-site updates of the saturated state (layer A order)."""
+    from oracle.tebd import TEBD as OracleTEBD
+    B, lam, _ = seed_state
+    o = OracleTEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
+                   eps_rel=WL.eps_rel)
+    o.set_state(B, lam)
+    triples = [j for j in range(1, WL.L - 1) if j % 3 == 1]
+    gates = [o.gate(j, WL.dt / 2) for j in triples]  # built before timing (host setup, not the path)
+    t0 = time.perf_counter()
+    for q in range(n_gates):
+        k = (q + 3) % len(triples)  # interior triples first
+        o.apply_gate(triples[k] - 1, gates[k])
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    state = workloads.synthetic_state(WL.L, WL.d, WL.chi_max)
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle_sample(per_step, state)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_sample(per_step, state)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config("fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} three-site updates of the saturated chi=256 state per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2401_05301_gb300 import TEBD
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    prec = 1 if args.precision == "mixed" else 0
+
+    B, lam, chi = workloads.synthetic_state(WL.L, WL.d, WL.chi_max, seed=workloads.SEED + rank)
+    g = TEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
+             eps_rel=WL.eps_rel, precision=prec, stream=stream.cuda_stream)
+    g.set_state(B, lam)
+    for _ in range(args.warmup):
+        g.step(1)
+        g.measure()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # -- device-timed region ------------------------------------------------------
+    g.set_option("profile", 1)
+    _, l0 = g.counters()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.step(1)
+            g.measure()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    _, l1 = g.counters()
+    prof = g.profile()
+    g.set_option("profile", 0)
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = GATES_PER_STEP * args.steps * ws / (t_max / 1e3)
+
+    # -- end to end through the C ABI with host buffers ---------------------------
+    pinned_B = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory().numpy() for b in B]
+    pinned_l = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy() for x in lam]
+    h2d = sum(b.nbytes for b in pinned_B) + sum(x.nbytes for x in pinned_l)
+    d2h = 8 * (WL.L + WL.L - 1)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.set_state(pinned_B, pinned_l)
+        g.step(1)
+        g.measure()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = GATES_PER_STEP * e2e_steps * ws / e2e_s
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # -- roofline of the dominant kernel class ---------------------------------------
+    dom = max((k for k in prof if k != "measure"), key=lambda k: prof[k][0])
+    dms, dlaunch, dwork = prof[dom]
+    achieved = dwork / (dms / 1e3) / 1e12 if dms > 0 else None
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 CUDA-core rate)",
+                "share_of_step": dms / ms if ms > 0 else None,
+                "classes_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                "classes_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] > 0 and v[2] > 0 else None)
+                                   for k, v in prof.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_cpu = 4
+        secs = oracle_sample(n_cpu, (B, lam, chi))
+        cpu = {"value": n_cpu / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n_cpu} three-site updates of the saturated chi=256 state ({secs:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+tf32x3",
+            "data": "synthetic", "config": config(args.precision),
+            "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+            "roofline": roofline, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

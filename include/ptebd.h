@@ -1,0 +1,160 @@
+/*
+ * ptebd.h - C ABI of the GB300 three-site TEBD library (libptebd.so).
+ *
+ * The library evolves a matrix product state in Vidal Gamma-lambda form
+ * (stored as B_j = Gamma_j lambda_j, right canonical) under a second-order
+ * Trotter split of the Bose-Hubbard chain with NN hopping J, NNN hopping
+ * J_NNN, on-site U and a harmonic trap K about j_c (arXiv:2401.05301,
+ * eq. (1)).  Each Trotter layer applies three-site gates exp(-i h_j tau) to
+ * all triples (j, j+1, j+2) with the same j mod 3 at once; every local update
+ * contracts theta, applies the gate, takes two truncated SVDs and rebuilds
+ * B and lambda (Sec. II B).  Densities n_j (eq. (8)) and currents
+ * 2 J Im <b+_j b_{j+1}> (eq. (5)) are measured from the canonical form.
+ *
+ * Conventions for every call:
+ *   - Sites are 1-based in the physics (j = 1..L, j_c in the same coordinate);
+ *     arrays passed across this ABI are 0-based C arrays over j = 1..L.
+ *   - Time is in units of hbar/J (the paper's Sec. I A sets J = hbar = 1).
+ *   - Every call returns a status (TEBD_OK = 0 or a negative TEBD_ERR_*),
+ *     never throws, and never keeps a pointer the caller passed in.
+ *   - All device memory is allocated and owned by the library, at
+ *     tebd_create (state, gates) and at the first tebd_step (workspace).
+ *   - A CUDA error puts the handle into a sticky error state: every later call
+ *     except tebd_destroy / tebd_strerror returns TEBD_ERR_CUDA.
+ *   - A handle is not thread safe; one handle issues work on one stream.
+ */
+#ifndef PTEBD_H
+#define PTEBD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tebd_ctx* tebd_handle;
+
+enum {
+  TEBD_OK = 0,
+  TEBD_ERR_ARG = -1,           /* invalid argument (range, NULL, non-finite) */
+  TEBD_ERR_OOM = -2,           /* device allocation failed */
+  TEBD_ERR_CUDA = -3,          /* CUDA runtime error (sticky) */
+  TEBD_ERR_STATE = -4,         /* call out of order (e.g. step before init) */
+  TEBD_ERR_NOT_CONVERGED = -5, /* eigen-solver iteration limit reached */
+  TEBD_ERR_TIMEOUT = -6,       /* bounded device wait ran out */
+  TEBD_ERR_NONFINITE = -7      /* NaN/Inf found in singular values */
+};
+
+/* Create a simulation of eq. (1) on L sites.
+ *   L >= 3 (three-site gates), 1 <= n_max <= 7 (local dimension d = n_max+1),
+ *   chi_max >= 1 (bond-dimension cap), U, J, J_NNN, K, j_c, dt finite, dt > 0.
+ * Builds the (L-2) x 2 gates exp(-i h_j tau), tau in {dt/2, dt}, on the host
+ * in FP64 (h_j: the three-site share of eq. (1), see tebd_gate_host), uploads
+ * them, and allocates the MPS on the current CUDA device.  The state is
+ * undefined until tebd_init_product.  *out receives the handle (NULL on error). */
+int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K,
+                double j_c, double dt, tebd_handle* out);
+
+/* Set a numerical option; valid before or between steps.
+ *   "w_cut"   discarded-weight cut: keep the fewest values whose discarded
+ *             weight sum_{i>chi'} p_i <= w_cut, p_i = s_i^2 / sum s^2  (default 0)
+ *   "eps_rel" drop every value with p_i <= eps_rel (default 1e-12, the paper's eps)
+ *   "precision" 0 = FP64 everywhere (default); 1 = mixed: theta/gate/rebuild
+ *             contractions as 3xTF32 on tensor cores, SVD stage in FP64
+ *   "max_slots" cap on triples processed concurrently (0 = automatic)
+ * Unknown key or out-of-range value: TEBD_ERR_ARG. */
+int tebd_set_option(tebd_handle h, const char* key, double value);
+
+/* Issue all work on the given cudaStream_t (NULL = legacy default stream).
+ * The stream must belong to the handle's device and outlive its use. */
+int tebd_set_stream(tebd_handle h, void* cuda_stream);
+
+/* Reset the state to the product state |occ[0], ..., occ[L-1]> (eq. (2) form),
+ * 0 <= occ[j] <= n_max; resets t, the step counter and w_total.  occ is a host
+ * array of L ints, read before the call returns. */
+int tebd_init_product(tebd_handle h, const int* occ);
+
+/* Apply n_steps >= 0 full second-order steps A(dt/2) B(dt/2) C(dt) B(dt/2) A(dt/2),
+ * where layer A holds the triples j = 1 mod 3, B: j = 2 mod 3, C: j = 0 mod 3.
+ * Work is enqueued on the handle's stream; the call returns after the last
+ * truncation decision of the last layer has been read back (the host needs
+ * the new bond dimensions to size the next launches). */
+int tebd_step(tebd_handle h, int n_steps);
+
+/* Apply one Trotter layer only: every triple j = residue + 1 (mod 3), 1-based
+ * (residue in {0, 1, 2}), with tau = dt/2 (full = 0) or dt (full = 1).  The
+ * step counter and t are unchanged.  Used to compare single layers of large
+ * states against a reference. */
+int tebd_layer(tebd_handle h, int residue, int full);
+
+/* Measure n_j (j = 1..L) into n_out[L] and current_j = 2 J Im <b+_j b_{j+1}>
+ * (j = 1..L-1, positive = flow from j to j+1) into cur_out[L-1], both host
+ * arrays of doubles owned by the caller.  Either pointer may be NULL to skip
+ * it.  Synchronises the handle's stream. */
+int tebd_measure(tebd_handle h, double* n_out, double* cur_out);
+
+/* Current time t = steps * dt, accumulated discarded weight w_total
+ * (sum of w over every truncation, Appendix B), and the largest bond
+ * dimension.  Any pointer may be NULL. */
+int tebd_stats(tebd_handle h, double* t, double* w_total, int* max_chi);
+
+/* Copy the bond dimensions chi_k, k = 0..L (chi_0 = chi_L = 1), into chi[L+1]. */
+int tebd_bond_dims(tebd_handle h, int* chi);
+
+/* Read back site k (0-based) as B[chi_k][d][chi_{k+1}] (complex FP64, real and
+ * imaginary interleaved: 2 * chi_k * d * chi_{k+1} doubles) and/or the bond
+ * vector lambda_k (chi_k doubles, k = 0..L).  Host buffers owned by the caller,
+ * sized from tebd_bond_dims; either pointer may be NULL. */
+int tebd_get_site(tebd_handle h, int k, double* B, double* lam);
+
+/* Install a state: site tensors B_k (host, interleaved complex, shape
+ * chi[k] x d x chi[k+1]) and bond vectors lam_k (host, chi[k] doubles,
+ * k = 0..L), with chi[0] = chi[L] = 1 and chi[k] <= min(chi_max, d^k, d^(L-k)).
+ * B_ptrs has L entries, lam_ptrs has L+1.  Resets t, steps and w_total.
+ * Used to start from a saturated state. */
+int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs,
+                   const double* const* lam_ptrs);
+
+/* Number of local updates (three-site gates) applied since init, and the
+ * number of CUDA kernels this handle has launched since create. */
+int tebd_counters(tebd_handle h, long long* gate_updates, long long* kernel_launches);
+
+/* Kernel classes timed when the option "profile" is 1. */
+enum {
+  TEBD_PROF_CONTRACT = 0, /* theta~ = B B B, gate, rebuild of B (complex GEMMs) */
+  TEBD_PROF_GRAM = 1,     /* Gram matrices theta' theta'^+ */
+  TEBD_PROF_TRIDIAG = 2,  /* Householder reduction of the Gram to tridiagonal form */
+  TEBD_PROF_BISECT = 3,   /* eigenvalues by bisection */
+  TEBD_PROF_EIGVEC = 4,   /* inverse iteration, orthonormalisation, back-transformation */
+  TEBD_PROF_PROJECT = 5,  /* Y = U^+ theta' (singular values and right vectors) */
+  TEBD_PROF_TRUNCATE = 6, /* sort, truncation rule, row gathers */
+  TEBD_PROF_MEASURE = 7,  /* densities and currents */
+  TEBD_PROF_NCLASS = 8
+};
+
+/* Totals since the option "profile" was last set to 1: device time in ms (CUDA
+ * events on the handle's stream around each group of launches), kernel launches,
+ * and algorithmic work (real FP64 flops for classes 0-5, with the Hermitian
+ * Gram counted at half and the tridiagonal reduction at 16/3 m^3; bytes of the
+ * site tensors read once for class 7).  Any output pointer may be NULL. */
+int tebd_profile(tebd_handle h, int cls, double* ms, long long* launches, double* work);
+
+/* Release everything the handle owns.  NULL is accepted. */
+void tebd_destroy(tebd_handle h);
+
+/* Static description of a status code. */
+const char* tebd_strerror(int status);
+
+/* Host-only helper (no GPU needed): the FP64 gate exp(-i h_j tau) of triple
+ * j (1-based, 1 <= j <= L-2) as a d^3 x d^3 row-major complex matrix with
+ * basis index s1*d^2 + s2*d + s3, written interleaved into out[2*d^6].
+ * h_j holds the NNN hop of the triple with weight 1, each NN hop (k,k+1)
+ * inside it divided by the number of triples containing that bond, and each
+ * on-site term U/2 n(n-1) + K/2 (k-j_c)^2 n divided by the number of triples
+ * containing site k, so that sum_j h_j equals eq. (1).  The exponential uses
+ * the library's own Hermitian Jacobi eigen-solver. */
+int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
+                   int j, double tau, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTEBD_H */

@@ -1,0 +1,922 @@
+// C ABI of the three-site TEBD library: handle, device state, and the host
+// orchestration of one Trotter layer (all triples with the same start mod 3
+// processed as one batch of independent local updates).
+#include "ptebd.h"
+#include "ptebd_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace ptebd;
+
+namespace {
+
+constexpr int MAX_SLOTS = 24;
+constexpr int MEAS_CHUNK = GEMM_MAXP;
+
+struct Slot {
+  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *U;
+  double *d, *e, *evals, *Z, *Z2, *S, *work, *s_sorted, *scal;  // scal: [0] trace [1] norm [2] w
+  int *perm, *chi;
+};
+
+struct Triple {
+  int i;        // 0-based first site
+  int slot;
+  int chl, c1, c2, chr;
+  int m1, n1, K1, chi1, m2, n2, K2, chi2;
+  double norm1, norm2, w1, w2;
+};
+
+}  // namespace
+
+struct tebd_ctx {
+  int L = 0, n_max = 0, d = 0, D = 0, chi_max = 0;
+  double U = 0, J = 0, Jnnn = 0, K = 0, jc = 0, dt = 0;
+  double w_cut = 0.0, eps_rel = 1e-12;
+  int precision = 0, max_slots = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sticky = TEBD_OK;
+  bool have_state = false;
+  std::vector<int> cap, chi;
+  std::vector<double2*> B;
+  std::vector<double*> lam;
+  double2* G = nullptr;
+  double2** dB = nullptr;
+  double** dlam = nullptr;
+  int* d_status = nullptr;
+  int* d_occ = nullptr;
+  std::vector<Slot> slots;
+  long long capmax = 0, mmax = 0, n1max = 0, kcap = 0;
+  double* h_pinned = nullptr;
+  size_t h_pinned_n = 0;
+  double2 *mP = nullptr, *mQ = nullptr, *mX = nullptr, *mY = nullptr, *mC = nullptr;
+  double* mN = nullptr;
+  double w_total = 0.0;
+  long long steps = 0, gate_updates = 0, launches = 0;
+  std::vector<void*> allocs;
+  // optional per-class timing (CUDA events on the handle's stream)
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[TEBD_PROF_NCLASS];
+  std::vector<int> prof_pending_cls;
+  double prof_ms[TEBD_PROF_NCLASS] = {};
+  long long prof_launches[TEBD_PROF_NCLASS] = {};
+  double prof_work[TEBD_PROF_NCLASS] = {};
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+cudaEvent_t get_event(tebd_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold every finished event pair into the per-class totals (call after a sync).
+void prof_collect(tebd_ctx* c) {
+  for (int k = 0; k < TEBD_PROF_NCLASS; ++k) {
+    for (auto& pr : c->prof_pending[k]) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->prof_ms[k] += ms;
+      c->event_pool.push_back(pr.first);
+      c->event_pool.push_back(pr.second);
+    }
+    c->prof_pending[k].clear();
+  }
+  cudaGetLastError();
+}
+
+// Times the launches issued during its lifetime as one interval of class cls.
+struct ProfScope {
+  tebd_ctx* c;
+  int cls;
+  long long l0;
+  cudaEvent_t a = nullptr;
+  ProfScope(tebd_ctx* c_, int cls_, double work) : c(c_), cls(cls_), l0(c_->launches) {
+    if (!c->prof) return;
+    c->prof_work[cls] += work;
+    a = get_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  ~ProfScope() {
+    if (!c->prof) return;
+    cudaEvent_t b = get_event(c);
+    cudaEventRecord(b, c->stream);
+    c->prof_pending[cls].push_back({a, b});
+    c->prof_launches[cls] += c->launches - l0;
+  }
+};
+
+template <typename T>
+T* dalloc(tebd_ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  c->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+int fail_cuda(tebd_ctx* c) {
+  c->sticky = TEBD_ERR_CUDA;
+  return TEBD_ERR_CUDA;
+}
+
+int check_launch(tebd_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "ptebd: CUDA error %s\n", cudaGetErrorString(e));
+    return fail_cuda(c);
+  }
+  return TEBD_OK;
+}
+
+void prof_collect(tebd_ctx* c);
+
+int sync(tebd_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "ptebd: CUDA error %s\n", cudaGetErrorString(e));
+    return fail_cuda(c);
+  }
+  if (c->prof) prof_collect(c);
+  return TEBD_OK;
+}
+
+long long ipow_cap(int d, int e, long long cap) {
+  long long v = 1;
+  for (int i = 0; i < e; ++i) {
+    v *= d;
+    if (v >= cap) return cap;
+  }
+  return std::min(v, cap);
+}
+
+int ensure_pinned(tebd_ctx* c, size_t n) {
+  if (c->h_pinned_n >= n) return TEBD_OK;
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  c->h_pinned = nullptr;
+  c->h_pinned_n = 0;
+  if (cudaMallocHost(&c->h_pinned, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return TEBD_ERR_OOM;
+  }
+  c->h_pinned_n = n;
+  return TEBD_OK;
+}
+
+int max_triples_per_layer(int L) {
+  int best = 0;
+  for (int r = 0; r < 3; ++r) {
+    int n = 0;
+    for (int i = r; i + 2 < L; i += 3) ++n;
+    best = std::max(best, n);
+  }
+  return best;
+}
+
+int alloc_workspace(tebd_ctx* c) {
+  if (!c->slots.empty()) return TEBD_OK;
+  const long long d = c->d, D = c->D;
+  long long capmax = 1;
+  for (int v : c->cap) capmax = std::max<long long>(capmax, v);
+  c->capmax = capmax;
+  c->mmax = capmax * d;
+  c->n1max = d * d * capmax;
+  c->kcap = std::min<long long>(c->mmax, c->chi_max);
+  if (c->mmax > 12288) return TEBD_ERR_ARG;  // Householder stage stages one column in shared memory
+  const long long mm = c->mmax, kc = c->kcap;
+  const double slot_bytes = 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm +
+                                    capmax * c->n1max + 3.0 * mm + EIG_PARTS + kc * mm) +
+                            8.0 * (4.0 * mm + 3 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
+  if (c->max_slots > 0) want = std::min(want, c->max_slots);
+  const int budget = (int)std::max(1.0, std::floor(0.8 * (double)free_b / slot_bytes));
+  const int nslots = std::max(1, std::min(want, budget));
+  for (int s = 0; s < nslots; ++s) {
+    Slot S{};
+    S.X = dalloc<double2>(c, capmax * d * d * capmax);
+    S.Th = dalloc<double2>(c, capmax * D * capmax);
+    S.Cb = dalloc<double2>(c, capmax * D * capmax);
+    S.H = dalloc<double2>(c, mm * mm);
+    S.V1h = dalloc<double2>(c, capmax * c->n1max);
+    S.tau = dalloc<double2>(c, mm);
+    S.part = dalloc<double2>(c, EIG_PARTS);
+    S.p = dalloc<double2>(c, mm);
+    S.U = dalloc<double2>(c, kc * mm);
+    S.d = dalloc<double>(c, mm);
+    S.e = dalloc<double>(c, mm);
+    S.evals = dalloc<double>(c, mm);
+    S.Z = dalloc<double>(c, mm * kc);
+    S.Z2 = dalloc<double>(c, mm * kc);
+    S.S = dalloc<double>(c, kc * kc);
+    S.work = dalloc<double>(c, 5 * mm * kc);
+    S.s_sorted = dalloc<double>(c, mm);
+    S.scal = dalloc<double>(c, 4);
+    S.perm = dalloc<int>(c, mm);
+    S.chi = dalloc<int>(c, 1);
+    if (!S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
+        !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
+      if (s == 0) return TEBD_ERR_OOM;
+      break;
+    }
+    c->slots.push_back(S);
+  }
+  return ensure_pinned(c, (size_t)c->slots.size() * (c->kcap + 8) + 64);
+}
+
+// PTEBD_DEBUG=1: synchronise after each stage and print a summary of a buffer
+// (finite count, max |x|) to stderr.  Diagnostic only; off by default.
+bool debug_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("PTEBD_DEBUG");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+void debug_dump(tebd_ctx* c, const char* label, int t, const void* ptr, size_t n_doubles) {
+  if (!debug_on()) return;
+  cudaStreamSynchronize(c->stream);
+  std::vector<double> h(n_doubles);
+  cudaMemcpy(h.data(), ptr, n_doubles * sizeof(double), cudaMemcpyDeviceToHost);
+  size_t bad = 0;
+  double mx = 0.0;
+  for (double x : h) {
+    if (!std::isfinite(x)) ++bad; else mx = std::max(mx, std::fabs(x));
+  }
+  std::fprintf(stderr, "[ptebd] %-10s t%d n=%zu nonfinite=%zu max=%.3e first=", label, t, n_doubles, bad, mx);
+  for (size_t i = 0; i < std::min<size_t>(n_doubles, 6); ++i) std::fprintf(stderr, "%.4e ", h[i]);
+  std::fprintf(stderr, "\n");
+}
+
+const double2* gate_ptr(const tebd_ctx* c, int i, int tidx) {
+  return c->G + ((size_t)tidx * (c->L - 2) + i) * (size_t)c->D * c->D;
+}
+
+// Eigen-decomposition of the Gram matrices held in the slots of ts (H, m, kmax
+// already set): trace, tridiagonal reduction, bisection, host choice of K,
+// eigenvectors.  On return the slots' U hold the K leading eigenvectors.
+int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
+  EigBatch eb{};
+  eb.n = (int)ts.size();
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const Slot& S = c->slots[ts[t].slot];
+    EigMat& M = eb.a[t];
+    M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p;
+    M.evals = S.evals; M.trace = S.scal; M.Z = S.Z; M.Z2 = S.Z2; M.S = S.S; M.work = S.work; M.U = S.U;
+    M.m = second ? ts[t].m2 : ts[t].m1;
+    const int n = second ? ts[t].n2 : ts[t].n1;
+    // at most min(m, n) singular values are non-zero: noise eigenvalues of a
+    // rank-deficient Gram matrix must never widen the bond beyond that
+    M.kmax = (int)std::min<long long>(std::min(M.m, n), c->chi_max);
+    M.K = 0;
+  }
+  {
+    double w = 0.0;
+    for (int t = 0; t < eb.n; ++t) w += 16.0 / 3.0 * std::pow((double)eb.a[t].m, 3);
+    ProfScope ps(c, TEBD_PROF_TRIDIAG, w);
+    c->launches += eig_trace(eb, c->stream);
+    c->launches += eig_tridiagonalize(eb, c->stream);
+  }
+  {
+    ProfScope ps(c, TEBD_PROF_BISECT, 0.0);
+    c->launches += eig_bisect(eb, c->stream);
+  }
+  if (int r = check_launch(c)) return r;
+  // read back the eigenvalues and the traces
+  const size_t stride = (size_t)c->kcap + 1;
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const EigMat& M = eb.a[t];
+    cudaMemcpyAsync(c->h_pinned + t * stride, M.evals, sizeof(double) * M.kmax, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(c->h_pinned + t * stride + c->kcap, M.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (int r = sync(c)) return r;
+  for (size_t t = 0; t < ts.size(); ++t) {
+    EigMat& M = eb.a[t];
+    const double* ev = c->h_pinned + t * stride;
+    const double trace = c->h_pinned[t * stride + c->kcap];
+    if (!is_fin(trace) || !(trace > 0.0)) {
+      c->sticky = TEBD_ERR_NONFINITE;
+      return TEBD_ERR_NONFINITE;
+    }
+    // eigenvectors for every eigenvalue that could pass the eps_rel floor (with a
+    // 100x margin for the Gram's rounding), at least one.  Below p ~ 1e-15 the
+    // Gram matrix's rounding (~eps_mach * trace) hides the singular values, so
+    // no vector is computed there whatever eps_rel says.
+    const double floor_v = std::max(0.01 * c->eps_rel, 1e-15) * trace;
+    int K = 0;
+    while (K < M.kmax && ev[K] > floor_v) ++K;
+    M.K = std::max(1, K);
+    if (second) ts[t].K2 = M.K; else ts[t].K1 = M.K;
+  }
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const EigMat& M = eb.a[t];
+    debug_dump(c, "d", ts[t].i, M.d, M.m);
+    debug_dump(c, "e", ts[t].i, M.e, M.m);
+    debug_dump(c, "evals", ts[t].i, M.evals, M.kmax);
+  }
+  {
+    double w = 0.0;
+    for (int t = 0; t < eb.n; ++t) {
+      const double m = eb.a[t].m, K = eb.a[t].K;
+      w += 8.0 * m * m * K + 12.0 * m * K * K;
+    }
+    ProfScope ps(c, TEBD_PROF_EIGVEC, w);
+    c->launches += eig_vectors(eb, c->stream);
+  }
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const EigMat& M = eb.a[t];
+    debug_dump(c, "Z", ts[t].i, M.Z, (size_t)M.m * M.K);
+    debug_dump(c, "Z2", ts[t].i, M.Z2, (size_t)M.m * M.K);
+    debug_dump(c, "U", ts[t].i, M.U, 2ull * M.m * M.K);
+    if (debug_on()) std::fprintf(stderr, "[ptebd] K=%d m=%d kmax=%d\n", M.K, M.m, M.kmax);
+  }
+  return check_launch(c);
+}
+
+int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
+  TruncBatch tb{};
+  tb.n = (int)ts.size();
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const Slot& S = c->slots[ts[t].slot];
+    TruncArgs& A = tb.a[t];
+    A.Y = S.Th;
+    A.K = second ? ts[t].K2 : ts[t].K1;
+    A.n = second ? ts[t].n2 : ts[t].n1;
+    A.trace = S.scal;
+    A.s_sorted = S.s_sorted;
+    A.perm = S.perm;
+    A.lam_out = c->lam[ts[t].i + (second ? 2 : 1)];
+    A.chi_out = S.chi;
+    A.norm_out = S.scal + 1;
+    A.w_out = S.scal + 2;
+    A.w_total = nullptr;
+    A.chi_max = std::min(c->chi_max, c->cap[ts[t].i + (second ? 2 : 1)]);
+    A.w_cut = c->w_cut;
+    A.eps_rel = c->eps_rel;
+    A.status = c->d_status;
+  }
+  {
+    ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
+    c->launches += launch_truncate(tb, c->stream);
+  }
+  // chi_max above is also the bond capacity, so chi' can never overrun lam or B
+  if (int r = check_launch(c)) return r;
+  const size_t stride = 4;
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const Slot& S = c->slots[ts[t].slot];
+    cudaMemcpyAsync(c->h_pinned + t * stride, S.scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(reinterpret_cast<int*>(c->h_pinned + t * stride + 2), S.chi, sizeof(int), cudaMemcpyDeviceToHost,
+                    c->stream);
+  }
+  int* h_status = reinterpret_cast<int*>(c->h_pinned + ts.size() * stride);
+  cudaMemcpyAsync(h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (int r = sync(c)) return r;
+  if (*h_status != 0) {
+    c->sticky = *h_status;
+    return *h_status;
+  }
+  for (size_t t = 0; t < ts.size(); ++t) {
+    const double* h = c->h_pinned + t * stride;
+    const int chi = *reinterpret_cast<const int*>(h + 2);
+    if (chi < 1 || chi > c->cap[ts[t].i + (second ? 2 : 1)]) {
+      c->sticky = TEBD_ERR_STATE;
+      return TEBD_ERR_STATE;
+    }
+    if (second) { ts[t].norm2 = h[0]; ts[t].w2 = h[1]; ts[t].chi2 = chi; }
+    else { ts[t].norm1 = h[0]; ts[t].w1 = h[1]; ts[t].chi1 = chi; }
+  }
+  return TEBD_OK;
+}
+
+// One batch of independent local updates (disjoint triples), FP64 path.
+int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
+  const int d = c->d, D = c->D;
+  cudaStream_t s = c->stream;
+  for (auto& T : ts) {
+    T.chl = c->chi[T.i]; T.c1 = c->chi[T.i + 1]; T.c2 = c->chi[T.i + 2]; T.chr = c->chi[T.i + 3];
+    T.m1 = T.chl * d;
+    T.n1 = d * d * T.chr;
+  }
+  // theta~ = B_i B_{i+1} B_{i+2}; C = G theta~; Gram H1 = (lam C)(lam C)^+
+  {
+    Gemm g1(true, OP_N, OP_N), g2(true, OP_N, OP_N), g3(true, OP_N, OP_N), g4(true, OP_N, OP_C);
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      g1.add(T.chl * d, d * T.c2, T.c1, c->B[T.i], T.c1, c->B[T.i + 1], (long long)d * T.c2, S.X, (long long)d * T.c2);
+      g2.add(T.chl * d * d, d * T.chr, T.c2, S.X, T.c2, c->B[T.i + 2], (long long)d * T.chr, S.Th, (long long)d * T.chr);
+      GemmProb& p3 = g3.add(D, T.chr, D, gate_ptr(c, T.i, tidx), D, S.Th, T.chr, S.Cb, T.chr);
+      p3.batch = T.chl;
+      p3.sA = 0;
+      p3.sB = p3.sC = (long long)D * T.chr;
+      GemmProb& p4 = g4.add(T.m1, T.m1, T.n1, S.Cb, T.n1, S.Cb, T.n1, S.H, T.m1);
+      p4.s_row = p4.s_col = c->lam[T.i];
+      p4.row_div = p4.col_div = d;
+    }
+    double wc = 0.0, wg = 0.0;
+    for (auto& T : ts) {
+      wc += 8.0 * ((double)T.chl * d * d * T.c2 * T.c1 + (double)T.chl * d * d * d * T.chr * T.c2 +
+                   (double)D * D * T.chr * T.chl);
+      wg += 4.0 * (double)T.m1 * T.m1 * T.n1;
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
+      c->launches += g1.launch(s, c->precision == 1);
+      c->launches += g2.launch(s, c->precision == 1);
+      c->launches += g3.launch(s, c->precision == 1);
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_GRAM, wg);
+      c->launches += g4.launch(s);
+    }
+    if (int r = check_launch(c)) return r;
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      debug_dump(c, "X", T.i, S.X, 2ull * T.chl * d * d * T.c2);
+      debug_dump(c, "Theta", T.i, S.Th, 2ull * T.m1 * T.n1);
+      debug_dump(c, "C", T.i, S.Cb, 2ull * T.m1 * T.n1);
+      debug_dump(c, "H1", T.i, S.H, 2ull * T.m1 * T.m1);
+    }
+  }
+  if (int r = eigen_stage(c, ts, false)) return r;
+  {  // Y1 = U1^+ (lam C)
+    Gemm g5(true, OP_CJ, OP_N);
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      GemmProb& p = g5.add(T.K1, T.n1, T.m1, S.U, T.m1, S.Cb, T.n1, S.Th, T.n1);
+      p.s_red = c->lam[T.i];
+      p.red_div = d;
+    }
+    double w = 0.0;
+    for (auto& T : ts) w += 8.0 * (double)T.K1 * T.n1 * T.m1;
+    ProfScope ps(c, TEBD_PROF_PROJECT, w);
+    c->launches += g5.launch(s);
+  }
+  for (auto& T : ts) debug_dump(c, "Y1", T.i, c->slots[T.slot].Th, 2ull * T.K1 * T.n1);
+  if (int r = truncate_stage(c, ts, false)) return r;
+  {
+    std::vector<GatherArgs> ga;
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      ga.push_back(GatherArgs{S.Th, S.perm, S.s_sorted, S.V1h, T.chi1, T.n1});
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
+      c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
+    }
+    // B_i = C V1 / ||s||;  Gram H2 = (lam' V1^+)(lam' V1^+)^+ viewed as (chi' d) x (d chr)
+    Gemm g6(true, OP_N, OP_C), g7(true, OP_N, OP_C);
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      T.m2 = T.chi1 * d;
+      T.n2 = d * T.chr;
+      GemmProb& p6 = g6.add(T.m1, T.chi1, T.n1, S.Cb, T.n1, S.V1h, T.n1, c->B[T.i], T.chi1);
+      p6.alpha_re = 1.0 / T.norm1;
+      GemmProb& p7 = g7.add(T.m2, T.m2, T.n2, S.V1h, T.n2, S.V1h, T.n2, S.H, T.m2);
+      p7.s_row = p7.s_col = c->lam[T.i + 1];
+      p7.row_div = p7.col_div = d;
+    }
+    double wc = 0.0, wg = 0.0;
+    for (auto& T : ts) {
+      wc += 8.0 * (double)T.m1 * T.chi1 * T.n1;
+      wg += 4.0 * (double)T.m2 * T.m2 * T.n2;
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
+      c->launches += g6.launch(s, c->precision == 1);
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_GRAM, wg);
+      c->launches += g7.launch(s);
+    }
+    if (int r = check_launch(c)) return r;
+  }
+  if (int r = eigen_stage(c, ts, true)) return r;
+  {  // Y2 = U2^+ (lam' V1^+)
+    Gemm g8(true, OP_CJ, OP_N);
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      GemmProb& p = g8.add(T.K2, T.n2, T.m2, S.U, T.m2, S.V1h, T.n2, S.Th, T.n2);
+      p.s_red = c->lam[T.i + 1];
+      p.red_div = d;
+    }
+    double w = 0.0;
+    for (auto& T : ts) w += 8.0 * (double)T.K2 * T.n2 * T.m2;
+    ProfScope ps(c, TEBD_PROF_PROJECT, w);
+    c->launches += g8.launch(s);
+  }
+  if (int r = truncate_stage(c, ts, true)) return r;
+  {
+    std::vector<GatherArgs> ga;
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      ga.push_back(GatherArgs{S.Th, S.perm, S.s_sorted, c->B[T.i + 2], T.chi2, T.n2});
+    }
+    {
+      ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
+      c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
+    }
+    // B_{i+1} = V1^+ V2 / ||s2||,  B_{i+2} = V2^+ (gathered above)
+    Gemm g9(true, OP_N, OP_C);
+    for (auto& T : ts) {
+      const Slot& S = c->slots[T.slot];
+      GemmProb& p = g9.add(T.m2, T.chi2, T.n2, S.V1h, T.n2, c->B[T.i + 2], T.n2, c->B[T.i + 1], T.chi2);
+      p.alpha_re = 1.0 / T.norm2;
+    }
+    double w = 0.0;
+    for (auto& T : ts) w += 8.0 * (double)T.m2 * T.chi2 * T.n2;
+    {
+      ProfScope ps(c, TEBD_PROF_CONTRACT, w);
+      c->launches += g9.launch(s, c->precision == 1);
+    }
+    if (int r = check_launch(c)) return r;
+  }
+  for (auto& T : ts) {
+    c->chi[T.i + 1] = T.chi1;
+    c->chi[T.i + 2] = T.chi2;
+    c->w_total += T.w1 + T.w2;
+    c->gate_updates += 1;
+  }
+  return TEBD_OK;
+}
+
+int run_layer(tebd_ctx* c, int residue, int tidx) {
+  std::vector<int> starts;
+  for (int i = residue; i + 2 < c->L; i += 3) starts.push_back(i);
+  const int ns = (int)c->slots.size();
+  for (size_t k0 = 0; k0 < starts.size(); k0 += ns) {
+    std::vector<Triple> ts;
+    for (size_t k = k0; k < std::min(starts.size(), k0 + ns); ++k) {
+      Triple T{};
+      T.i = starts[k];
+      T.slot = (int)(k - k0);
+      ts.push_back(T);
+    }
+    if (int r = update_chunk(c, ts, tidx)) return r;
+  }
+  return TEBD_OK;
+}
+
+int ensure_measure_ws(tebd_ctx* c) {
+  if (c->mN) return TEBD_OK;
+  const long long capmax = std::max<long long>(1, *std::max_element(c->cap.begin(), c->cap.end()));
+  const long long big = capmax * c->d * capmax;
+  c->mP = dalloc<double2>(c, MEAS_CHUNK * big);
+  c->mQ = dalloc<double2>(c, MEAS_CHUNK * big);
+  c->mX = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
+  c->mY = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
+  c->mC = dalloc<double2>(c, c->L);
+  c->mN = dalloc<double>(c, c->L);
+  if (!c->mP || !c->mQ || !c->mX || !c->mY || !c->mC || !c->mN) return TEBD_ERR_OOM;
+  return TEBD_OK;
+}
+
+#define CHECK_HANDLE(h)                         \
+  do {                                          \
+    if (!(h)) return TEBD_ERR_ARG;              \
+    if ((h)->sticky != TEBD_OK) return (h)->sticky; \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+const char* tebd_strerror(int status) {
+  switch (status) {
+    case TEBD_OK: return "ok";
+    case TEBD_ERR_ARG: return "invalid argument";
+    case TEBD_ERR_OOM: return "device allocation failed";
+    case TEBD_ERR_CUDA: return "CUDA error";
+    case TEBD_ERR_STATE: return "call out of order";
+    case TEBD_ERR_NOT_CONVERGED: return "iteration limit reached";
+    case TEBD_ERR_TIMEOUT: return "device wait timed out";
+    case TEBD_ERR_NONFINITE: return "non-finite singular values";
+    default: return "unknown status";
+  }
+}
+
+int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c, int j, double tau,
+                   double* out) {
+  if (L < 3 || n_max < 1 || n_max > 7 || j < 1 || j > L - 2 || !out) return TEBD_ERR_ARG;
+  if (!is_fin(U) || !is_fin(J) || !is_fin(J_NNN) || !is_fin(K) || !is_fin(j_c) || !is_fin(tau)) return TEBD_ERR_ARG;
+  try {
+    std::vector<std::complex<double>> G;
+    if (!build_gate(L, n_max, U, J, J_NNN, K, j_c, j, tau, G)) return TEBD_ERR_NOT_CONVERGED;
+    std::memcpy(out, G.data(), G.size() * sizeof(std::complex<double>));
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return TEBD_OK;
+}
+
+int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K, double j_c, double dt,
+                tebd_handle* out) {
+  if (!out) return TEBD_ERR_ARG;
+  *out = nullptr;
+  if (L < 3 || n_max < 1 || n_max > 7 || chi_max < 1) return TEBD_ERR_ARG;
+  if (!is_fin(U) || !is_fin(J) || !is_fin(J_NNN) || !is_fin(K) || !is_fin(j_c) || !is_fin(dt) || !(dt > 0))
+    return TEBD_ERR_ARG;
+  tebd_ctx* c = nullptr;
+  try {
+    c = new tebd_ctx();
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  c->L = L; c->n_max = n_max; c->d = n_max + 1; c->D = c->d * c->d * c->d; c->chi_max = chi_max;
+  c->U = U; c->J = J; c->Jnnn = J_NNN; c->K = K; c->jc = j_c; c->dt = dt;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return TEBD_ERR_CUDA;
+  }
+  try {
+    c->cap.resize(L + 1);
+    for (int k = 0; k <= L; ++k) c->cap[k] = (int)ipow_cap(c->d, std::min(k, L - k), chi_max);
+    c->chi.assign(L + 1, 1);
+    c->B.resize(L);
+    c->lam.resize(L + 1);
+    for (int k = 0; k < L; ++k) {
+      c->B[k] = dalloc<double2>(c, (size_t)c->cap[k] * c->d * c->cap[k + 1]);
+      if (!c->B[k]) throw std::bad_alloc();
+    }
+    for (int k = 0; k <= L; ++k) {
+      c->lam[k] = dalloc<double>(c, c->cap[k]);
+      if (!c->lam[k]) throw std::bad_alloc();
+    }
+    c->dB = dalloc<double2*>(c, L);
+    c->dlam = dalloc<double*>(c, L + 1);
+    c->d_status = dalloc<int>(c, 1);
+    c->d_occ = dalloc<int>(c, L);
+    const size_t DD = (size_t)c->D * c->D;
+    c->G = dalloc<double2>(c, 2 * (size_t)(L - 2) * DD);
+    if (!c->dB || !c->dlam || !c->d_status || !c->d_occ || !c->G) throw std::bad_alloc();
+    std::vector<std::complex<double>> Gall(2 * (size_t)(L - 2) * DD), Gj;
+    for (int t = 0; t < 2; ++t)
+      for (int j = 1; j <= L - 2; ++j) {
+        const double tau = (t == 0) ? 0.5 * dt : dt;
+        if (!build_gate(L, n_max, U, J, J_NNN, K, j_c, j, tau, Gj)) {
+          tebd_destroy(c);
+          return TEBD_ERR_NOT_CONVERGED;
+        }
+        std::copy(Gj.begin(), Gj.end(), Gall.begin() + ((size_t)t * (L - 2) + (j - 1)) * DD);
+      }
+    if (cudaMemcpy(c->G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->dB, c->B.data(), L * sizeof(double2*), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->dlam, c->lam.data(), (L + 1) * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      tebd_destroy(c);
+      return TEBD_ERR_CUDA;
+    }
+  } catch (...) {
+    tebd_destroy(c);
+    return TEBD_ERR_OOM;
+  }
+  *out = c;
+  return TEBD_OK;
+}
+
+int tebd_set_option(tebd_handle h, const char* key, double value) {
+  CHECK_HANDLE(h);
+  if (!key || !is_fin(value)) return TEBD_ERR_ARG;
+  const std::string k(key);
+  if (k == "w_cut") {
+    if (value < 0 || value >= 1) return TEBD_ERR_ARG;
+    h->w_cut = value;
+  } else if (k == "eps_rel") {
+    if (value < 0 || value >= 1) return TEBD_ERR_ARG;
+    h->eps_rel = value;
+  } else if (k == "precision") {
+    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    h->precision = (int)value;
+  } else if (k == "profile") {
+    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
+    prof_collect(h);
+    h->prof = (value == 1.0);
+    for (int q = 0; q < TEBD_PROF_NCLASS; ++q) {
+      h->prof_ms[q] = 0.0;
+      h->prof_launches[q] = 0;
+      h->prof_work[q] = 0.0;
+    }
+  } else if (k == "max_slots") {
+    if (value < 0 || value > MAX_SLOTS || value != std::floor(value)) return TEBD_ERR_ARG;
+    if (!h->slots.empty()) return TEBD_ERR_STATE;
+    h->max_slots = (int)value;
+  } else {
+    return TEBD_ERR_ARG;
+  }
+  return TEBD_OK;
+}
+
+int tebd_set_stream(tebd_handle h, void* cuda_stream) {
+  CHECK_HANDLE(h);
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TEBD_OK;
+}
+
+int tebd_init_product(tebd_handle h, const int* occ) {
+  CHECK_HANDLE(h);
+  if (!occ) return TEBD_ERR_ARG;
+  for (int k = 0; k < h->L; ++k)
+    if (occ[k] < 0 || occ[k] > h->n_max) return TEBD_ERR_ARG;
+  if (cudaMemcpyAsync(h->d_occ, occ, h->L * sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return fail_cuda(h);
+  h->launches += launch_init_product(h->dB, h->dlam, h->d_occ, h->L, h->d, h->stream);
+  if (int r = check_launch(h)) return r;
+  if (int r = sync(h)) return r;  // occ is pageable caller memory
+  std::fill(h->chi.begin(), h->chi.end(), 1);
+  h->steps = 0;
+  h->w_total = 0.0;
+  h->gate_updates = 0;
+  h->have_state = true;
+  return TEBD_OK;
+}
+
+int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs, const double* const* lam_ptrs) {
+  CHECK_HANDLE(h);
+  if (!chi || !B_ptrs || !lam_ptrs) return TEBD_ERR_ARG;
+  if (chi[0] != 1 || chi[h->L] != 1) return TEBD_ERR_ARG;
+  for (int k = 0; k <= h->L; ++k)
+    if (chi[k] < 1 || chi[k] > h->cap[k]) return TEBD_ERR_ARG;
+  for (int k = 0; k < h->L; ++k) {
+    if (!B_ptrs[k]) return TEBD_ERR_ARG;
+    const size_t n = (size_t)chi[k] * h->d * chi[k + 1];
+    if (cudaMemcpy(h->B[k], B_ptrs[k], n * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) return fail_cuda(h);
+  }
+  for (int k = 0; k <= h->L; ++k) {
+    if (!lam_ptrs[k]) return TEBD_ERR_ARG;
+    if (cudaMemcpy(h->lam[k], lam_ptrs[k], chi[k] * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail_cuda(h);
+  }
+  h->chi.assign(chi, chi + h->L + 1);
+  h->steps = 0;
+  h->w_total = 0.0;
+  h->gate_updates = 0;
+  h->have_state = true;
+  return TEBD_OK;
+}
+
+int tebd_step(tebd_handle h, int n_steps) {
+  CHECK_HANDLE(h);
+  if (n_steps < 0) return TEBD_ERR_ARG;
+  if (!h->have_state) return TEBD_ERR_STATE;
+  if (n_steps == 0) return TEBD_OK;
+  try {
+    if (int r = alloc_workspace(h)) return r;
+    // A(dt/2) B(dt/2) C(dt) B(dt/2) A(dt/2); residue r <-> triples j = r+1 mod 3
+    const int sched[5][2] = {{0, 0}, {1, 0}, {2, 1}, {1, 0}, {0, 0}};
+    for (int n = 0; n < n_steps; ++n) {
+      for (int l = 0; l < 5; ++l)
+        if (int r = run_layer(h, sched[l][0], sched[l][1])) return r;
+      h->steps += 1;
+    }
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return TEBD_OK;
+}
+
+int tebd_layer(tebd_handle h, int residue, int full) {
+  CHECK_HANDLE(h);
+  if (residue < 0 || residue > 2 || (full != 0 && full != 1)) return TEBD_ERR_ARG;
+  if (!h->have_state) return TEBD_ERR_STATE;
+  try {
+    if (int r = alloc_workspace(h)) return r;
+    return run_layer(h, residue, full);
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+}
+
+int tebd_measure(tebd_handle h, double* n_out, double* cur_out) {
+  CHECK_HANDLE(h);
+  if (!h->have_state) return TEBD_ERR_STATE;
+  try {
+    if (int r = ensure_measure_ws(h)) return r;
+    const int L = h->L, d = h->d;
+    double mbytes = 0.0;
+    for (int k = 0; k < L; ++k) mbytes += 16.0 * h->chi[k] * d * h->chi[k + 1];
+    ProfScope ps(h, TEBD_PROF_MEASURE, mbytes);
+    std::vector<DensityArgs> da(L);
+    for (int k = 0; k < L; ++k) da[k] = DensityArgs{h->B[k], h->lam[k], h->mN + k, h->chi[k], d, h->chi[k + 1]};
+    h->launches += launch_densities(da.data(), L, h->stream);
+    const long long capmax = std::max<long long>(1, *std::max_element(h->cap.begin(), h->cap.end()));
+    const long long big = capmax * d * capmax;
+    for (int k0 = 0; k0 < L - 1; k0 += MEAS_CHUNK) {
+      const int k1 = std::min(L - 1, k0 + MEAS_CHUNK);
+      Gemm gx(true, OP_C, OP_N), gy(true, OP_N, OP_C);
+      for (int k = k0; k < k1; ++k) {
+        const int q = k - k0;
+        const int cl = h->chi[k], cm = h->chi[k + 1], cr = h->chi[k + 2];
+        double2* P = h->mP + q * big;
+        double2* Q = h->mQ + q * big;
+        h->launches += launch_shift_left(h->B[k], h->lam[k], P, cl, d, cm, h->stream);
+        h->launches += launch_shift_right(h->B[k + 1], Q, cm, d, cr, h->stream);
+        gx.add(cm, cm, cl * d, P, cm, h->B[k], cm, h->mX + q * capmax * capmax, cm);
+        gy.add(cm, cm, d * cr, Q, (long long)d * cr, h->B[k + 1], (long long)d * cr, h->mY + q * capmax * capmax, cm);
+      }
+      h->launches += gx.launch(h->stream);
+      h->launches += gy.launch(h->stream);
+      for (int k = k0; k < k1; ++k) {
+        const int q = k - k0;
+        h->launches += launch_trace_product(h->mX + q * capmax * capmax, h->mY + q * capmax * capmax, h->chi[k + 1],
+                                            h->mC + k, h->stream);
+      }
+    }
+    if (int r = check_launch(h)) return r;
+    if (int r = ensure_pinned(h, 3 * (size_t)L + 8)) return r;
+    cudaMemcpyAsync(h->h_pinned, h->mN, L * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(h->h_pinned + L, h->mC, (L - 1) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
+    if (int r = sync(h)) return r;
+    if (n_out) std::memcpy(n_out, h->h_pinned, L * sizeof(double));
+    if (cur_out)
+      for (int k = 0; k < L - 1; ++k) cur_out[k] = 2.0 * h->J * h->h_pinned[L + 2 * k + 1];
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return TEBD_OK;
+}
+
+int tebd_stats(tebd_handle h, double* t, double* w_total, int* max_chi) {
+  CHECK_HANDLE(h);
+  if (t) *t = (double)h->steps * h->dt;
+  if (w_total) *w_total = h->w_total;
+  if (max_chi) *max_chi = *std::max_element(h->chi.begin(), h->chi.end());
+  return TEBD_OK;
+}
+
+int tebd_bond_dims(tebd_handle h, int* chi) {
+  CHECK_HANDLE(h);
+  if (!chi) return TEBD_ERR_ARG;
+  std::copy(h->chi.begin(), h->chi.end(), chi);
+  return TEBD_OK;
+}
+
+int tebd_get_site(tebd_handle h, int k, double* B, double* lam) {
+  CHECK_HANDLE(h);
+  if (k < 0 || k > h->L) return TEBD_ERR_ARG;
+  if (B && k == h->L) return TEBD_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
+  if (B) {
+    const size_t n = (size_t)h->chi[k] * h->d * h->chi[k + 1];
+    if (cudaMemcpy(B, h->B[k], n * sizeof(double2), cudaMemcpyDeviceToHost) != cudaSuccess) return fail_cuda(h);
+  }
+  if (lam && cudaMemcpy(lam, h->lam[k], h->chi[k] * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail_cuda(h);
+  return TEBD_OK;
+}
+
+int tebd_profile(tebd_handle h, int cls, double* ms, long long* launches, double* work) {
+  CHECK_HANDLE(h);
+  if (cls < 0 || cls >= TEBD_PROF_NCLASS) return TEBD_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
+  prof_collect(h);
+  if (ms) *ms = h->prof_ms[cls];
+  if (launches) *launches = h->prof_launches[cls];
+  if (work) *work = h->prof_work[cls];
+  return TEBD_OK;
+}
+
+int tebd_counters(tebd_handle h, long long* gate_updates, long long* kernel_launches) {
+  CHECK_HANDLE(h);
+  if (gate_updates) *gate_updates = h->gate_updates;
+  if (kernel_launches) *kernel_launches = h->launches;
+  return TEBD_OK;
+}
+
+void tebd_destroy(tebd_handle h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  prof_collect(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  cudaGetLastError();
+  delete h;
+}
+
+}  // extern "C"

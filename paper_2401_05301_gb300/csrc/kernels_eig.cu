@@ -1,0 +1,541 @@
+// FP64 Hermitian eigen-solver for batches of Gram matrices H = theta' theta'^+.
+//
+// The truncated SVD of every local update (Sec. II B) is taken through the
+// Gram matrix: its eigenvectors are the left singular vectors of theta'.
+// Stages (each batched over all triples of a layer):
+//   1. Householder reduction H = Q T Q^+ with T real symmetric tridiagonal
+//      (reflectors H(k) = I - tau_k v_k v_k^+ with real beta_k, so the
+//      sub-diagonal is real); one column per step, three kernels per step.
+//   2. Bisection on Sturm counts for the kmax largest eigenvalues of T.
+//   3. Inverse iteration for the K kept eigenvalues (one thread per
+//      eigenvector, LU with partial pivoting of T - lambda I), with
+//      Gram-Schmidt inside groups of nearly equal eigenvalues.
+//   4. Newton-Schulz orthonormalisation Z <- Z (3I - Z^T Z)/2, three rounds.
+//   5. Back-transformation U = Q Z, one block per pair of eigenvectors.
+// All reductions use a fixed order, so results are bitwise reproducible.
+#include "ptebd_internal.h"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <vector>
+
+namespace ptebd {
+
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+__device__ __forceinline__ double2 warp_sum2(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
+
+// Sum over the block (blockDim.x a multiple of 32, <= 1024); every thread gets the result.
+__device__ double block_sum(double v, double* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < nw) ? sh[l] : 0.0;
+    t = warp_sum(t);
+    if (l == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__device__ double block_min(double v, double* sh) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < nw) ? sh[l] : DBL_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (l == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+constexpr int NT = 256;
+
+// ---- trace --------------------------------------------------------------------
+__global__ void k_trace(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.x];
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (int r = threadIdx.x; r < M.m; r += blockDim.x) s += M.H[(size_t)r * M.m + r].x;
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *M.trace = s;
+}
+
+// ---- Householder reduction ------------------------------------------------------
+// Column k (taken as the conjugate of row k, which is contiguous): build the
+// reflector with H^+ (alpha, x) = (beta, 0), beta real, and store v (v_0 = 1)
+// in row k beyond the diagonal.
+__global__ void k_house(const __grid_constant__ EigBatch b, int k) {
+  const EigMat& M = b.a[blockIdx.x];
+  const int m = M.m;
+  if (k >= m) return;
+  double2* row = M.H + (size_t)k * m;
+  if (k == m - 1) {
+    if (threadIdx.x == 0) {
+      M.d[k] = row[k].x;
+      M.e[k] = 0.0;
+      M.tau[k] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
+  const int n = m - k - 1;
+  double2* x = row + k + 1;
+  __shared__ double sh[33];
+  __shared__ double2 scale_sh;
+  // Scale by the largest component first, so that squares of tiny entries
+  // (rank-deficient Gram matrices reach 1e-160 and below) cannot underflow.
+  double amax = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
+  amax = -block_min(-amax, sh);
+  const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
+  double s = 0.0;
+  for (int r = 1 + threadIdx.x; r < n; r += blockDim.x) {
+    const double vx = x[r].x * sinv, vy = x[r].y * sinv;
+    s = fma(vx, vx, fma(vy, vy, s));
+  }
+  const double xnorm2 = block_sum(s, sh);  // of the scaled column
+  if (threadIdx.x == 0) {
+    const double ar = x[0].x * sinv, ai = -x[0].y * sinv;  // scaled alpha = conj(row[k+1])
+    double beta;
+    double2 tau, scale;
+    if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
+      beta = x[0].x;
+      tau = make_double2(0.0, 0.0);
+      scale = make_double2(0.0, 0.0);
+    } else {
+      const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
+      tau = make_double2((bs - ar) / bs, -ai / bs);
+      const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
+      scale = make_double2(zr / den * sinv, -zi / den * sinv);  // 1 / (alpha - beta)
+      beta = bs * amax;
+    }
+    M.d[k] = row[k].x;
+    M.e[k] = beta;
+    M.tau[k] = tau;
+    scale_sh = scale;
+  }
+  __syncthreads();
+  const double2 sc = scale_sh;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    x[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(x[r]), sc);
+  }
+}
+
+// p = tau * A22 v, and per-block partial sums of p^+ v.
+__global__ void k_hemv(const __grid_constant__ EigBatch b, int k) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m;
+  if (k >= m - 1) return;
+  const int n = m - k - 1;
+  extern __shared__ double2 vs[];
+  const double2* v = M.H + (size_t)k * m + k + 1;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) vs[r] = v[r];
+  __syncthreads();
+  const double2 tau = M.tau[k];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2 part = make_double2(0.0, 0.0);
+  for (int r = blockIdx.x * nw + warp; r < n; r += gridDim.x * nw) {
+    const double2* Arow = M.H + (size_t)(k + 1 + r) * m + k + 1;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = lane; c < n; c += 32) acc = cfma(Arow[c], vs[c], acc);
+    acc = warp_sum2(acc);
+    const double2 p = cmul(tau, acc);
+    if (lane == 0) {
+      M.p[r] = p;
+      part = cfma_conj(p, vs[r], part);
+    }
+  }
+  __shared__ double2 sh[32];
+  if (lane == 0) sh[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < nw; ++w) t = cadd(t, sh[w]);
+    M.part[blockIdx.x] = t;
+  }
+}
+
+// A22 <- A22 - v w^+ - w v^+,  w = p + alpha v,  alpha = -tau (p^+ v) / 2.
+__global__ void k_rank2(const __grid_constant__ EigBatch b, int k, int nparts) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m;
+  if (k >= m - 1) return;
+  const int n = m - k - 1;
+  const double2 tau = M.tau[k];
+  double2 dot = make_double2(0.0, 0.0);
+  for (int g = 0; g < nparts; ++g) dot = cadd(dot, M.part[g]);
+  const double2 t2 = cmul(tau, dot);
+  const double2 alpha = make_double2(-0.5 * t2.x, -0.5 * t2.y);
+  const double2* v = M.H + (size_t)k * m + k + 1;
+  const double2* p = M.p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = blockIdx.x * nw + warp; r < n; r += gridDim.x * nw) {
+    const double2 vr = v[r];
+    const double2 wr = cfma(alpha, vr, p[r]);
+    double2* Arow = M.H + (size_t)(k + 1 + r) * m + k + 1;
+    for (int c = lane; c < n; c += 32) {
+      const double2 vc = v[c];
+      const double2 wc = cfma(alpha, vc, p[c]);
+      double2 a = Arow[c];
+      // a -= vr * conj(wc) + wr * conj(vc)
+      a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
+      a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
+      Arow[c] = a;
+    }
+  }
+}
+
+// ---- bisection --------------------------------------------------------------------
+__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += (q < 0.0);
+  for (int i = 1; i < m; ++i) {
+    const double ei = e[i - 1];
+    q = d[i] - x - (ei * ei) / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.0);
+  }
+  return cnt;
+}
+
+__device__ void gershgorin(const double* d, const double* e, int m, double* sh, double& gl, double& gu) {
+  double lo = DBL_MAX, hi = DBL_MAX;  // hi stored negated for a min-reduction
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double r = 0.0;
+    if (i > 0) r += fabs(e[i - 1]);
+    if (i < m - 1) r += fabs(e[i]);
+    lo = fmin(lo, d[i] - r);
+    hi = fmin(hi, -(d[i] + r));
+  }
+  gl = block_min(lo, sh);
+  gu = -block_min(hi, sh);
+}
+
+__global__ void k_bisect(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m;
+  __shared__ double sh[33];
+  double gl, gu;
+  gershgorin(M.d, M.e, m, sh, gl, gu);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M.kmax || j >= m) return;
+  const double bnorm = fmax(fabs(gl), fabs(gu));
+  const double pivmin = DBL_MIN * fmax(1.0, bnorm * bnorm);
+  const double eps = DBL_EPSILON;
+  double lo = gl - 2.0 * eps * bnorm * m - 4.0 * pivmin;
+  double hi = gu + 2.0 * eps * bnorm * m + 4.0 * pivmin;
+  const double atol = 2.0 * eps * bnorm + 4.0 * pivmin;
+  const int target = m - 1 - j;  // ascending index of the j-th largest
+  for (int it = 0; it < 200; ++it) {
+    if (hi - lo <= atol) break;
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(M.d, M.e, m, mid, pivmin) > target) hi = mid; else lo = mid;
+  }
+  M.evals[j] = 0.5 * (lo + hi);
+}
+
+// ---- inverse iteration ----------------------------------------------------------------
+__device__ __forceinline__ double hash_uniform(unsigned long long a, unsigned long long b) {
+  unsigned long long z = a * 0x9E3779B97F4A7C15ull + b * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+// LU with partial pivoting of T - sigma I (tridiagonal; one fill-in diagonal).
+// Row i of U: (u0, u1, u2) at columns (i, i+1, i+2); l = multiplier; piv = 1 if rows swapped.
+__device__ void tri_lu(const double* d, const double* e, int m, double sigma, double tiny, double* U0, double* U1,
+                       double* U2, double* Lm, double* Pv, int ld) {
+  double u = d[0] - sigma, v = (m > 1) ? e[0] : 0.0, w = 0.0;
+  for (int i = 0; i < m - 1; ++i) {
+    const double c = e[i];                       // sub-diagonal entry of row i+1
+    const double a = d[i + 1] - sigma;           // diagonal of row i+1
+    const double bb = (i + 1 < m - 1) ? e[i + 1] : 0.0;  // super-diagonal of row i+1
+    if (fabs(c) > fabs(u)) {
+      const double l = u / c;
+      U0[(size_t)i * ld] = c; U1[(size_t)i * ld] = a; U2[(size_t)i * ld] = bb;
+      Lm[(size_t)i * ld] = l; Pv[(size_t)i * ld] = 1.0;
+      const double nu = v - l * a, nv = w - l * bb;
+      u = nu; v = nv; w = 0.0;
+    } else {
+      if (u == 0.0) u = tiny;
+      const double l = c / u;
+      U0[(size_t)i * ld] = u; U1[(size_t)i * ld] = v; U2[(size_t)i * ld] = w;
+      Lm[(size_t)i * ld] = l; Pv[(size_t)i * ld] = 0.0;
+      const double nu = a - l * v, nv = bb - l * w;
+      u = nu; v = nv; w = 0.0;
+    }
+    if (fabs(U0[(size_t)i * ld]) < tiny) U0[(size_t)i * ld] = copysign(tiny, U0[(size_t)i * ld]);
+  }
+  if (fabs(u) < tiny) u = copysign(tiny, u);
+  U0[(size_t)(m - 1) * ld] = u; U1[(size_t)(m - 1) * ld] = 0.0; U2[(size_t)(m - 1) * ld] = 0.0;
+}
+
+__device__ void tri_solve(int m, const double* U0, const double* U1, const double* U2, const double* Lm,
+                          const double* Pv, int ld, double* z) {
+  // forward: apply the row operations of the factorisation to z
+  double cur = z[0];
+  for (int i = 0; i < m - 1; ++i) {
+    const double nxt = z[(size_t)(i + 1) * ld];
+    const double l = Lm[(size_t)i * ld];
+    if (Pv[(size_t)i * ld] != 0.0) {
+      z[(size_t)i * ld] = nxt;
+      cur = cur - l * nxt;
+    } else {
+      z[(size_t)i * ld] = cur;
+      cur = nxt - l * cur;
+    }
+  }
+  z[(size_t)(m - 1) * ld] = cur;
+  // back substitution
+  double z1 = 0.0, z2 = 0.0;  // z[i+1], z[i+2]
+  for (int i = m - 1; i >= 0; --i) {
+    const double zi = (z[(size_t)i * ld] - U1[(size_t)i * ld] * z1 - U2[(size_t)i * ld] * z2) / U0[(size_t)i * ld];
+    z[(size_t)i * ld] = zi;
+    z2 = z1;
+    z1 = zi;
+  }
+}
+
+__global__ void k_inviter(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m, K = M.K;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= K) return;
+  const double* ev = M.evals;
+  double tnorm = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double r = fabs(M.d[i]);
+    if (i > 0) r += fabs(M.e[i - 1]);
+    if (i < m - 1) r += fabs(M.e[i]);
+    tnorm = fmax(tnorm, r);
+  }
+  if (tnorm == 0.0) tnorm = 1.0;
+  // Bisection places each shift within ~2 eps tnorm of its eigenvalue; eigenvalues
+  // closer than 100x that are treated as one group and orthogonalised explicitly.
+  const double gtol = 200.0 * DBL_EPSILON * tnorm;
+  if (j > 0 && ev[j - 1] - ev[j] <= gtol) return;  // not the first of its group
+  int g = j + 1;
+  while (g < K && ev[g - 1] - ev[g] <= gtol) ++g;
+  const double tiny = DBL_EPSILON * tnorm;
+  const int ld = K;
+  for (int q = j; q < g; ++q) {
+    double* U0 = M.work + q;
+    double* U1 = U0 + (size_t)m * K;
+    double* U2 = U1 + (size_t)m * K;
+    double* Lm = U2 + (size_t)m * K;
+    double* Pv = Lm + (size_t)m * K;
+    tri_lu(M.d, M.e, m, ev[q], tiny, U0, U1, U2, Lm, Pv, ld);
+    double* z = M.Z + q;
+    for (int i = 0; i < m; ++i) z[(size_t)i * ld] = hash_uniform(q + 1, i + 1);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve(m, U0, U1, U2, Lm, Pv, ld, z);
+      double mx = 0.0;
+      for (int i = 0; i < m; ++i) mx = fmax(mx, fabs(z[(size_t)i * ld]));
+      const double inv = (mx > 0.0) ? 1.0 / mx : 1.0;
+      for (int i = 0; i < m; ++i) z[(size_t)i * ld] *= inv;
+      for (int p = j; p < q; ++p) {  // Gram-Schmidt against earlier group members
+        const double* y = M.Z + p;
+        double dot = 0.0;
+        for (int i = 0; i < m; ++i) dot = fma(y[(size_t)i * ld], z[(size_t)i * ld], dot);
+        for (int i = 0; i < m; ++i) z[(size_t)i * ld] -= dot * y[(size_t)i * ld];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) nrm = fma(z[(size_t)i * ld], z[(size_t)i * ld], nrm);
+      nrm = sqrt(nrm);
+      const double s = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+      for (int i = 0; i < m; ++i) z[(size_t)i * ld] *= s;
+    }
+  }
+}
+
+// S <- 1.5 I - 0.5 S
+__global__ void k_ns_form(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int K = M.K;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < K * K; idx += gridDim.x * blockDim.x) {
+    const int r = idx / K, c = idx % K;
+    M.S[idx] = (r == c ? 1.5 : 0.0) - 0.5 * M.S[idx];
+  }
+}
+
+// U[j][r] = Z[r][j] (real -> complex, transposed).
+__global__ void k_z_to_u(const __grid_constant__ EigBatch b, int use_z2) {
+  const EigMat& M = b.a[blockIdx.z];
+  const int m = M.m, K = M.K;
+  __shared__ double tile[32][33];
+  const double* Z = use_z2 ? M.Z2 : M.Z;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  if (r0 >= m || c0 >= K) return;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < m && c < K) ? Z[(size_t)r * K + c] : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < K && r < m) M.U[(size_t)c * m + r] = make_double2(tile[threadIdx.x][i], 0.0);
+  }
+}
+
+constexpr int CPB = 2;  // eigenvectors per block in the back-transformation
+
+__global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m, K = M.K;
+  const int c0 = blockIdx.x * CPB;
+  if (c0 >= K) return;
+  const int ncol = min(CPB, K - c0);
+  __shared__ double sh[33];
+  for (int k = m - 2; k >= 0; --k) {
+    const double2 tau = M.tau[k];
+    if (tau.x == 0.0 && tau.y == 0.0) continue;
+    const int n = m - k - 1;
+    const double2* v = M.H + (size_t)k * m + k + 1;
+    double2 w[CPB];
+    for (int cc = 0; cc < CPB; ++cc) {
+      double2 acc = make_double2(0.0, 0.0);
+      if (cc < ncol) {
+        const double2* u = M.U + (size_t)(c0 + cc) * m + k + 1;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) acc = cfma_conj(v[r], u[r], acc);
+      }
+      acc.x = block_sum(acc.x, sh);
+      acc.y = block_sum(acc.y, sh);
+      w[cc] = cmul(tau, acc);
+    }
+    for (int cc = 0; cc < ncol; ++cc) {
+      double2* u = M.U + (size_t)(c0 + cc) * m + k + 1;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) u[r] = csub(u[r], cmul(v[r], w[cc]));
+    }
+    __syncthreads();
+  }
+}
+
+int max_m(const EigBatch& b) {
+  int mm = 0;
+  for (int i = 0; i < b.n; ++i) mm = std::max(mm, b.a[i].m);
+  return mm;
+}
+
+}  // namespace
+
+static_assert(sizeof(EigBatch) < 4000, "kernel parameter block too large");
+
+int eig_trace(const EigBatch& b, cudaStream_t s) {
+  if (b.n == 0) return 0;
+  k_trace<<<b.n, NT, 0, s>>>(b);
+  return 1;
+}
+
+int eig_tridiagonalize(const EigBatch& b, cudaStream_t s) {
+  if (b.n == 0) return 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_hemv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const int mm = max_m(b);
+  int launches = 0;
+  for (int k = 0; k < mm; ++k) {
+    k_house<<<b.n, NT, 0, s>>>(b, k);
+    ++launches;
+    const int n = mm - k - 1;
+    if (n <= 0) continue;
+    const int G = std::max(1, std::min({(n + 7) / 8, EIG_PARTS, std::max(1, 1216 / b.n)}));
+    const size_t smem = (size_t)n * sizeof(double2);
+    k_hemv<<<dim3(G, b.n), NT, smem, s>>>(b, k);
+    k_rank2<<<dim3(G, b.n), NT, 0, s>>>(b, k, G);
+    launches += 2;
+  }
+  return launches;
+}
+
+int eig_bisect(const EigBatch& b, cudaStream_t s) {
+  if (b.n == 0) return 0;
+  int km = 0;
+  for (int i = 0; i < b.n; ++i) km = std::max(km, std::min(b.a[i].kmax, b.a[i].m));
+  if (km == 0) return 0;
+  k_bisect<<<dim3((km + 127) / 128, b.n), 128, 0, s>>>(b);
+  return 1;
+}
+
+int eig_vectors(const EigBatch& b0, cudaStream_t s) {
+  if (b0.n == 0) return 0;
+  EigBatch b = b0;
+  int Kmax = 0, launches = 0;
+  for (int i = 0; i < b.n; ++i) Kmax = std::max(Kmax, b.a[i].K);
+  if (Kmax == 0) return 0;
+  k_inviter<<<dim3((Kmax + 63) / 64, b.n), 64, 0, s>>>(b);
+  ++launches;
+  // Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z)
+  bool in_z2 = false;
+  for (int it = 0; it < 3; ++it) {
+    Gemm g1(false, OP_C, OP_N), g2(false, OP_N, OP_N);
+    for (int i = 0; i < b.n; ++i) {
+      const EigMat& M = b.a[i];
+      if (M.K == 0) continue;
+      const double* Zc = in_z2 ? M.Z2 : M.Z;
+      g1.add(M.K, M.K, M.m, Zc, M.K, Zc, M.K, M.S, M.K);
+    }
+    launches += g1.launch(s);
+    k_ns_form<<<dim3(std::max(1, std::min(64, (Kmax * Kmax + 255) / 256)), b.n), 256, 0, s>>>(b);
+    ++launches;
+    for (int i = 0; i < b.n; ++i) {
+      const EigMat& M = b.a[i];
+      if (M.K == 0) continue;
+      const double* Zc = in_z2 ? M.Z2 : M.Z;
+      double* Zn = in_z2 ? M.Z : M.Z2;
+      g2.add(M.m, M.K, M.K, Zc, M.K, M.S, M.K, Zn, M.K);
+    }
+    launches += g2.launch(s);
+    in_z2 = !in_z2;
+  }
+  const int mm = max_m(b);
+  k_z_to_u<<<dim3((mm + 31) / 32, (Kmax + 31) / 32, b.n), dim3(32, 8), 0, s>>>(b, in_z2 ? 1 : 0);
+  ++launches;
+  k_backtransform<<<dim3((Kmax + CPB - 1) / CPB, b.n), NT, 0, s>>>(b);
+  ++launches;
+  return launches;
+}
+
+}  // namespace ptebd

@@ -1,0 +1,150 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <complex>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace ptebd {
+
+// ---- host gate builder (gates_host.cpp) --------------------------------------
+std::vector<std::complex<double>> three_site_term(int L, int n_max, double U, double J, double Jnnn,
+                                                  double K, double jc, int j);
+bool build_gate(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int j,
+                double tau, std::vector<std::complex<double>>& G);
+
+// ---- grouped GEMM (kernels_gemm.cu) ------------------------------------------
+// C = alpha * op(A) * op(B) [+ C], op in {N, C = conjugate transpose, CJ = conjugate}; complex
+// (double2) or real (double).  Up to GEMM_MAXP independent problems, each
+// optionally strided-batched, share one launch.  Optional scalings:
+//   s_red[k / red_div]  multiplies A(i, k) along the reduction index,
+//   s_row[i / row_div], s_col[j / col_div] multiply the result.
+enum { OP_N = 0, OP_C = 1, OP_CJ = 2 };  // CJ: element-wise conjugate, no transpose
+constexpr int GEMM_MAXP = 16;
+
+struct GemmProb {
+  const void* A;
+  const void* B;
+  void* C;
+  long long lda, ldb, ldc, sA, sB, sC;
+  const double* s_red;
+  const double* s_row;
+  const double* s_col;
+  double alpha_re, alpha_im;
+  int M, N, K, batch;
+  int red_div, row_div, col_div, accumulate;
+};
+
+struct GemmBatch {
+  GemmProb p[GEMM_MAXP];
+  int tile_start[GEMM_MAXP + 1];
+  int nprob, opA, opB, mixed;
+};
+
+class Gemm {
+ public:
+  Gemm(bool complex_, int opA, int opB) : cplx_(complex_), opA_(opA), opB_(opB) {}
+  GemmProb& add(int M, int N, int K, const void* A, long long lda, const void* B, long long ldb, void* C,
+                long long ldc);
+  // Launch everything added so far (in chunks of GEMM_MAXP) on stream; returns launches issued.
+  int launch(cudaStream_t s, bool mixed = false);
+  size_t size() const { return probs_.size(); }
+
+ private:
+  bool cplx_;
+  int opA_, opB_;
+  std::vector<GemmProb> probs_;
+};
+
+// ---- eigen-solver for batches of Hermitian matrices (kernels_eig.cu) ---------
+constexpr int EIG_MAXP = 24;
+
+struct EigMat {
+  double2* H;        // m x m Hermitian (full storage), row-major, ld = m; reflectors end in rows
+  double* d;         // tridiagonal diagonal [m]
+  double* e;         // sub-diagonal [m]
+  double2* tau;      // Householder scalars [m]
+  double2* part;     // partial dot products [EIG_PARTS]
+  double2* p;        // hemv result [m]
+  double* evals;     // eigenvalues, descending [kmax]
+  double* trace;     // [1] trace of H (sum of Re H_rr), taken before reduction
+  double* Z;         // m x K real eigenvectors of T (row-major, ld = K)
+  double* Z2;        // m x K scratch (Newton-Schulz ping-pong)
+  double* S;         // K x K scratch
+  double* work;      // inverse-iteration LU scratch, 5 * m * K doubles
+  double2* U;        // K x m eigenvectors of H, one per row (U[j*m + r] = u_j[r])
+  int m, kmax, K;
+};
+
+struct EigBatch {
+  EigMat a[EIG_MAXP];
+  int n;
+};
+
+constexpr int EIG_PARTS = 256;  // max blocks in the hemv stage
+
+// Each returns the number of kernel launches issued.
+int eig_trace(const EigBatch& b, cudaStream_t s);
+int eig_tridiagonalize(const EigBatch& b, cudaStream_t s);
+int eig_bisect(const EigBatch& b, cudaStream_t s);
+// Inverse iteration on T for eigenvalues 0..K-1, Newton-Schulz orthonormalisation,
+// and back-transformation U = Q Z.  Reads a[i].K (set from the eigenvalues).
+int eig_vectors(const EigBatch& b, cudaStream_t s);
+
+// ---- small kernels (kernels_misc.cu) -------------------------------------------
+struct TruncArgs {
+  const double2* Y;  // K x n rows u_k^+ theta'
+  int K, n;
+  const double* trace;
+  double* s_sorted;   // [K] descending ||Y_k||
+  int* perm;          // [K]
+  double* lam_out;    // [chi'] s / ||s_kept||
+  int* chi_out;       // [1]
+  double* norm_out;   // [1] ||s_kept||
+  double* w_out;      // [1] discarded weight of this truncation
+  double* w_total;    // accumulated (device)
+  int chi_max;
+  double w_cut, eps_rel;
+  int* status;        // device status word
+};
+constexpr int TRUNC_MAXP = 24;
+struct TruncBatch {
+  TruncArgs a[TRUNC_MAXP];
+  int n;
+};
+int launch_truncate(const TruncBatch& b, cudaStream_t s);
+
+struct GatherArgs {
+  const double2* Y;
+  const int* perm;
+  const double* s_sorted;
+  double2* out;  // chi x n
+  int chi, n;
+};
+int launch_gather_rows(const GatherArgs* a, int n, cudaStream_t s);
+
+int launch_init_product(double2* const* B, double* const* lam, const int* occ_dev, int L, int d,
+                        cudaStream_t s);
+
+struct DensityArgs {
+  const double2* B;
+  const double* lam;
+  double* out;
+  int chl, d, chr;
+};
+int launch_densities(const DensityArgs* a, int n, cudaStream_t s);
+
+// P'[(a,s),c] = lam_a^2 sqrt(s+1) B[a,s+1,c] (s < d-1), 0 for s = d-1
+int launch_shift_left(const double2* B, const double* lam, double2* out, int chl, int d, int chr,
+                      cudaStream_t s);
+// Q'[c,(t,b)] = sqrt(t+1) B[c,t+1,b] (t < d-1), 0 for t = d-1
+int launch_shift_right(const double2* B, double2* out, int chl, int d, int chr, cudaStream_t s);
+// out = sum_{c,c'} X[c,c'] Yt[c',c]
+int launch_trace_product(const double2* X, const double2* Yt, int chi, double2* out, cudaStream_t s);
+
+int launch_check_finite(const double* x, int n, int* status, cudaStream_t s);
+
+}  // namespace ptebd

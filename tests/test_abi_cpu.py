@@ -1,0 +1,56 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every declared symbol,
+and its host-only gate builder matches the oracle (no GPU compute)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import model
+from paper_2401_05301_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2401_05301_gb300 import build
+    build.build()
+    return binding.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ptebd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tebd_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(binding.SIGNATURES)
+
+
+def test_strerror(lib):
+    assert lib.tebd_strerror(0) == b"ok"
+    assert lib.tebd_strerror(-7) == b"non-finite singular values"
+
+
+@pytest.mark.parametrize("n_max,L,j", [(1, 5, 1), (2, 6, 2), (3, 8, 3), (3, 8, 6), (4, 64, 30)])
+def test_host_gate_matches_oracle(lib, n_max, L, j):
+    U, J, Jnnn, K, jc = 5.0, 1.0, 0.1, 0.003, (L + 1) / 2
+    for tau in (0.005, 0.01):
+        G = binding.gate_host(L, n_max, U, J, Jnnn, K, jc, j, tau)
+        ref = model.gate(model.three_site_term(j, L, n_max, U, J, Jnnn, K, jc), tau)
+        assert np.max(np.abs(G - ref)) < 1e-13
+        assert np.max(np.abs(G.conj().T @ G - np.eye(len(G)))) < 1e-13
+
+
+def test_host_gate_rejects_bad_args(lib):
+    out = np.empty(2 * 64 ** 2)
+    ptr = out.ctypes.data_as(binding._P_double)
+    assert lib.tebd_gate_host(2, 3, 1, 1, 0, 0, 1, 1, 0.1, ptr) == -1   # L < 3
+    assert lib.tebd_gate_host(8, 3, 1, 1, 0, 0, 1, 7, 0.1, ptr) == -1   # j > L-2
+    assert lib.tebd_gate_host(8, 3, float("nan"), 1, 0, 0, 1, 1, 0.1, ptr) == -1
