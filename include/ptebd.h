@@ -40,7 +40,8 @@ enum {
   TEBD_ERR_STATE = -4,         /* call out of order (e.g. step before init) */
   TEBD_ERR_NOT_CONVERGED = -5, /* eigen-solver iteration limit reached */
   TEBD_ERR_TIMEOUT = -6,       /* bounded device wait ran out */
-  TEBD_ERR_NONFINITE = -7      /* NaN/Inf found in singular values */
+  TEBD_ERR_NONFINITE = -7,     /* NaN/Inf found in singular values */
+  TEBD_ERR_TOO_LARGE = -8      /* size beyond a fixed capacity (tebd_bond_correlator_noalloc) */
 };
 
 /* Create a simulation of eq. (1) on L sites.
@@ -153,6 +154,31 @@ const char* tebd_strerror(int status);
  * the library's own Hermitian Jacobi eigen-solver. */
 int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
                    int j, double tau, double* out);
+
+/* Allocation-free nearest-neighbour correlator of one bond.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the value (a fixed device-memory budget, a
+ * framework allocator that must own all device memory, or a latency-critical
+ * loop where cudaMalloc would synchronise the device).  It computes
+ *   C = <b+_j b_{j+1}> = sum conj(theta[a,s,t,b]) (b+ (x) b) theta[a,s',t',b],
+ *   theta = lam_left (.) B_left B_right,
+ * the same quantity tebd_measure turns into current_j = 2 J Im C.
+ * Inputs (device, caller-owned): B_left [chi_l][d][chi_m] and B_right
+ * [chi_m][d][chi_r] as interleaved complex doubles, lam_left [chi_l] doubles.
+ * Output (device, caller-owned): C_out[0] = Re C, C_out[1] = Im C.
+ * Work is enqueued on cuda_stream (NULL = legacy default stream); the call
+ * does not synchronise.  Limits: chi_l, chi_m, chi_r <= 64 and 2 <= d <= 8;
+ * larger sizes return TEBD_ERR_TOO_LARGE (with a message on stderr) and
+ * launch nothing.
+ * Memory: no cudaMalloc, cudaFree or other allocation.  Scratch is a fixed
+ * file-scope device array of about 1.2 MB, held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make this first call before any stream capture.  All calls on a device
+ * share the array, so calls that overlap on the GPU (different streams, or
+ * threads without ordering) race and give wrong results; serialise them. */
+int tebd_bond_correlator_noalloc(const double* B_left, const double* lam_left, const double* B_right,
+                                 int chi_l, int chi_m, int chi_r, int d, double* C_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -613,6 +613,7 @@ const char* tebd_strerror(int status) {
     case TEBD_ERR_NOT_CONVERGED: return "iteration limit reached";
     case TEBD_ERR_TIMEOUT: return "device wait timed out";
     case TEBD_ERR_NONFINITE: return "non-finite singular values";
+    case TEBD_ERR_TOO_LARGE: return "size exceeds the fixed scratch capacity";
     default: return "unknown status";
   }
 }

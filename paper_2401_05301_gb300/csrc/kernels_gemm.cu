@@ -157,6 +157,19 @@ GemmProb& Gemm::add(int M, int N, int K, const void* A, long long lda, const voi
   return probs_.back();
 }
 
+int gemm_launch_single(bool complex_, int opA, int opB, const GemmProb& p, cudaStream_t s) {
+  if (p.M <= 0 || p.N <= 0 || p.batch <= 0) return 0;
+  GemmBatch gb{};
+  gb.opA = opA;
+  gb.opB = opB;
+  gb.nprob = 1;
+  gb.p[0] = p;
+  gb.tile_start[0] = 0;
+  gb.tile_start[1] = p.batch * ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  if (complex_) dispatch<C>(gb, gb.tile_start[1], s); else dispatch<R>(gb, gb.tile_start[1], s);
+  return 1;
+}
+
 int Gemm::launch(cudaStream_t s, bool) {
   int launches = 0;
   size_t i = 0;

@@ -59,6 +59,9 @@ class Gemm {
   std::vector<GemmProb> probs_;
 };
 
+// One problem, launched without any host or device allocation.
+int gemm_launch_single(bool complex_, int opA, int opB, const GemmProb& p, cudaStream_t s);
+
 // ---- eigen-solver for batches of Hermitian matrices (kernels_eig.cu) ---------
 constexpr int EIG_MAXP = 24;
 
