@@ -34,7 +34,15 @@ if ROOT not in sys.path:
 import workloads  # noqa: E402
 
 WL = workloads.TRUNC_L32
-GATES_PER_STEP = 50  # A(10) + B(10) + C(10) + B(10) + A(10) for L = 32
+WORKLOADS = {"trunc_L32": workloads.TRUNC_L32, "parity_L8": workloads.PARITY_L8}
+
+
+def gates_per_step(L: int) -> int:
+    """Three-site gate updates in one A/2 B/2 C B/2 A/2 step (50 for L = 32)."""
+    n = {r: len(range(r, L - 2, 3)) for r in range(3)}
+    return 2 * n[0] + 2 * n[1] + n[2]
+
+
 METRIC = "TEBD gate-updates/s at chi_max"
 UNIT = "gate-updates/s"
 # FP64 on GB300: 152 SMs x 2 DFMA (4 flop) per clock x 2070 MHz (a DFMA throughput
@@ -43,9 +51,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
 
 def config(precision: str):
-    return {"workload": f"L{WL.L}_d{WL.d}_chi{WL.chi_max}_wcut1e-10_synthetic_saturated",
+    return {"workload": f"L{WL.L}_d{WL.d}_chi{WL.chi_max}_wcut{WL.w_cut:g}_synthetic_saturated",
             "L": WL.L, "d": WL.d, "chi_max": WL.chi_max, "dt": WL.dt, "precision": precision,
-            "step": "one 2nd-order Trotter step (50 three-site gate updates) + n_j/current measurement",
+            "step": f"one 2nd-order Trotter step ({gates_per_step(WL.L)} three-site gate updates) + n_j/current measurement",
             "l2_flush": "not needed: state + workspace > 2 GB > 129 MB L2"}
 
 
@@ -150,7 +158,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="trunc_L32", choices=sorted(WORKLOADS),
+                    help="trunc_L32 is the measured configuration; parity_L8 is a small case for profiling")
     args = ap.parse_args()
+    global WL
+    WL = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -200,7 +212,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = GATES_PER_STEP * args.steps * ws / (t_max / 1e3)
+    value = gates_per_step(WL.L) * args.steps * ws / (t_max / 1e3)
 
     # -- end to end through the C ABI with host buffers ---------------------------
     pinned_B = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory().numpy() for b in B]
@@ -221,7 +233,7 @@ def main():
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = GATES_PER_STEP * e2e_steps * ws / e2e_s
+    e2e_value = gates_per_step(WL.L) * e2e_steps * ws / e2e_s
 
     if rank != 0:
         if ws > 1:

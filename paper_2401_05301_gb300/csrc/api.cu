@@ -434,6 +434,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       GemmProb& p4 = g4.add(T.m1, T.m1, T.n1, S.Cb, T.n1, S.Cb, T.n1, S.H, T.m1);
       p4.s_row = p4.s_col = c->lam[T.i];
       p4.row_div = p4.col_div = d;
+      p4.herm = 1;
     }
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
@@ -497,6 +498,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       GemmProb& p7 = g7.add(T.m2, T.m2, T.n2, S.V1h, T.n2, S.V1h, T.n2, S.H, T.m2);
       p7.s_row = p7.s_col = c->lam[T.i + 1];
       p7.row_div = p7.col_div = d;
+      p7.herm = 1;
     }
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {

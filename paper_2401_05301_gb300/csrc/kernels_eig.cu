@@ -495,7 +495,7 @@ int eig_bisect(const EigBatch& b, cudaStream_t s) {
   int km = 0;
   for (int i = 0; i < b.n; ++i) km = std::max(km, std::min(b.a[i].kmax, b.a[i].m));
   if (km == 0) return 0;
-  k_bisect<<<dim3((km + 127) / 128, b.n), 128, 0, s>>>(b);
+  k_bisect<<<dim3((km + 31) / 32, b.n), 32, 0, s>>>(b);  // one warp per block spreads the chains over SMs
   return 1;
 }
 
@@ -505,7 +505,7 @@ int eig_vectors(const EigBatch& b0, cudaStream_t s) {
   int Kmax = 0, launches = 0;
   for (int i = 0; i < b.n; ++i) Kmax = std::max(Kmax, b.a[i].K);
   if (Kmax == 0) return 0;
-  k_inviter<<<dim3((Kmax + 63) / 64, b.n), 64, 0, s>>>(b);
+  k_inviter<<<dim3((Kmax + 31) / 32, b.n), 32, 0, s>>>(b);
   ++launches;
   // Newton-Schulz: Z <- Z (1.5 I - 0.5 Z^T Z)
   bool in_z2 = false;

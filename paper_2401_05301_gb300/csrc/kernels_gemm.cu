@@ -56,9 +56,18 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
   const GemmProb& P = gb.p[pi];
   const int local = tile - gb.tile_start[pi];
   const int tn = (P.N + BN - 1) / BN, tm = (P.M + BM - 1) / BM;
-  const int per_batch = tm * tn;
+  const int per_batch = P.herm ? tm * (tm + 1) / 2 : tm * tn;
   const int bidx = local / per_batch, r = local % per_batch;
-  const int bm = r / tn, bn = r % tn;
+  int bm, bn;
+  if (P.herm) {  // r enumerates the lower-triangular tiles row by row
+    bm = (int)((sqrt(8.0 * r + 1.0) - 1.0) * 0.5);
+    while (bm * (bm + 1) / 2 > r) --bm;
+    while ((bm + 1) * (bm + 2) / 2 <= r) ++bm;
+    bn = r - bm * (bm + 1) / 2;
+  } else {
+    bm = r / tn;
+    bn = r % tn;
+  }
   const T* __restrict__ A = static_cast<const T*>(P.A) + (long long)bidx * P.sA;
   const T* __restrict__ B = static_cast<const T*>(P.B) + (long long)bidx * P.sB;
   T* __restrict__ Cm = static_cast<T*>(P.C) + (long long)bidx * P.sC;
@@ -125,6 +134,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
       T v = A_::scale(A_::mul_alpha(acc[i][j], P.alpha_re, P.alpha_im), sr * sc);
       T* dst = Cm + (long long)gi * P.ldc + gj;
       *dst = P.accumulate ? A_::add(*dst, v) : v;
+      if (P.herm && bn < bm) {  // mirror an off-diagonal tile into the upper triangle
+        T* mir = Cm + (long long)gj * P.ldc + gi;
+        const T cv = A_::cj(v);
+        *mir = P.accumulate ? A_::add(*mir, cv) : cv;
+      }
     }
   }
 }
@@ -165,7 +179,8 @@ int gemm_launch_single(bool complex_, int opA, int opB, const GemmProb& p, cudaS
   gb.nprob = 1;
   gb.p[0] = p;
   gb.tile_start[0] = 0;
-  gb.tile_start[1] = p.batch * ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  const int tm = (p.M + BM - 1) / BM;
+  gb.tile_start[1] = p.batch * (p.herm ? tm * (tm + 1) / 2 : tm * ((p.N + BN - 1) / BN));
   if (complex_) dispatch<C>(gb, gb.tile_start[1], s); else dispatch<R>(gb, gb.tile_start[1], s);
   return 1;
 }
@@ -182,7 +197,8 @@ int Gemm::launch(cudaStream_t s, bool) {
       if (p.M <= 0 || p.N <= 0 || p.batch <= 0) continue;
       gb.p[gb.nprob] = p;
       gb.tile_start[gb.nprob] = tiles;
-      tiles += p.batch * ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+      const int tm = (p.M + BM - 1) / BM;
+      tiles += p.batch * (p.herm ? tm * (tm + 1) / 2 : tm * ((p.N + BN - 1) / BN));
       gb.nprob++;
     }
     gb.tile_start[gb.nprob] = tiles;

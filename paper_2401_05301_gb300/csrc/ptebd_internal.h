@@ -36,6 +36,7 @@ struct GemmProb {
   double alpha_re, alpha_im;
   int M, N, K, batch;
   int red_div, row_div, col_div, accumulate;
+  int herm;  // result is Hermitian (M == N, B = A^+): only lower tiles are computed, then mirrored
 };
 
 struct GemmBatch {
