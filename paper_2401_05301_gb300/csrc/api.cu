@@ -54,6 +54,7 @@ struct tebd_ctx {
   double** dlam = nullptr;
   int* d_status = nullptr;
   int* d_occ = nullptr;
+  unsigned int* d_bar = nullptr;  // grid-barrier state of the persistent reduction
   std::vector<Slot> slots;
   long long capmax = 0, mmax = 0, n1max = 0, kcap = 0;
   double* h_pinned = nullptr;
@@ -281,6 +282,7 @@ const double2* gate_ptr(const tebd_ctx* c, int i, int tidx) {
 int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   EigBatch eb{};
   eb.n = (int)ts.size();
+  eb.bar = c->d_bar;
   for (size_t t = 0; t < ts.size(); ++t) {
     const Slot& S = c->slots[ts[t].slot];
     EigMat& M = eb.a[t];
@@ -298,7 +300,13 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     for (int t = 0; t < eb.n; ++t) w += 16.0 / 3.0 * std::pow((double)eb.a[t].m, 3);
     ProfScope ps(c, TEBD_PROF_TRIDIAG, w);
     c->launches += eig_trace(eb, c->stream);
-    c->launches += eig_tridiagonalize(eb, c->stream);
+    const int nl = eig_tridiagonalize(eb, c->stream);
+    if (nl < 0) {
+      cudaGetLastError();
+      std::fprintf(stderr, "ptebd: cooperative launch of the tridiagonal reduction refused\n");
+      return fail_cuda(c);
+    }
+    c->launches += nl;
   }
   {
     ProfScope ps(c, TEBD_PROF_BISECT, 0.0);
@@ -312,7 +320,13 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     cudaMemcpyAsync(c->h_pinned + t * stride, M.evals, sizeof(double) * M.kmax, cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(c->h_pinned + t * stride + c->kcap, M.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   }
+  unsigned int* h_bar = reinterpret_cast<unsigned int*>(c->h_pinned + ts.size() * stride);
+  cudaMemcpyAsync(h_bar, c->d_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
   if (int r = sync(c)) return r;
+  if (*h_bar != 0) {  // a grid barrier of the reduction timed out: results are invalid
+    c->sticky = TEBD_ERR_TIMEOUT;
+    return TEBD_ERR_TIMEOUT;
+  }
   for (size_t t = 0; t < ts.size(); ++t) {
     EigMat& M = eb.a[t];
     const double* ev = c->h_pinned + t * stride;
@@ -672,9 +686,10 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
     c->dlam = dalloc<double*>(c, L + 1);
     c->d_status = dalloc<int>(c, 1);
     c->d_occ = dalloc<int>(c, L);
+    c->d_bar = dalloc<unsigned int>(c, 4);
     const size_t DD = (size_t)c->D * c->D;
     c->G = dalloc<double2>(c, 2 * (size_t)(L - 2) * DD);
-    if (!c->dB || !c->dlam || !c->d_status || !c->d_occ || !c->G) throw std::bad_alloc();
+    if (!c->dB || !c->dlam || !c->d_status || !c->d_occ || !c->d_bar || !c->G) throw std::bad_alloc();
     std::vector<std::complex<double>> Gall(2 * (size_t)(L - 2) * DD), Gj;
     for (int t = 0; t < 2; ++t)
       for (int j = 1; j <= L - 2; ++j) {
@@ -688,7 +703,8 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
     if (cudaMemcpy(c->G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->dB, c->B.data(), L * sizeof(double2*), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->dlam, c->lam.data(), (L + 1) * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)) != cudaSuccess) {
       cudaGetLastError();
       tebd_destroy(c);
       return TEBD_ERR_CUDA;

@@ -5,8 +5,8 @@
 // Stages (each batched over all triples of a layer):
 //   1. Householder reduction H = Q T Q^+ with T real symmetric tridiagonal
 //      (reflectors H(k) = I - tau_k v_k v_k^+ with real beta_k, so the
-//      sub-diagonal is real); one column per step, three kernels per step.
-//   2. Bisection on Sturm counts for the kmax largest eigenvalues of T.
+//      sub-diagonal is real), in one persistent cooperative launch.
+//   2. Bisection on (division-free) Sturm counts for the kmax largest eigenvalues of T.
 //   3. Inverse iteration for the K kept eigenvalues (one thread per
 //      eigenvector, LU with partial pivoting of T - lambda I), with
 //      Gram-Schmidt inside groups of nearly equal eigenvalues.
@@ -97,141 +97,27 @@ __global__ void k_trace(const __grid_constant__ EigBatch b) {
   if (threadIdx.x == 0) *M.trace = s;
 }
 
-// ---- Householder reduction ------------------------------------------------------
-// Column k (taken as the conjugate of row k, which is contiguous): build the
-// reflector with H^+ (alpha, x) = (beta, 0), beta real, and store v (v_0 = 1)
-// in row k beyond the diagonal.
-__global__ void k_house(const __grid_constant__ EigBatch b, int k) {
-  const EigMat& M = b.a[blockIdx.x];
-  const int m = M.m;
-  if (k >= m) return;
-  double2* row = M.H + (size_t)k * m;
-  if (k == m - 1) {
-    if (threadIdx.x == 0) {
-      M.d[k] = row[k].x;
-      M.e[k] = 0.0;
-      M.tau[k] = make_double2(0.0, 0.0);
-    }
-    return;
-  }
-  const int n = m - k - 1;
-  double2* x = row + k + 1;
-  __shared__ double sh[33];
-  __shared__ double2 scale_sh;
-  // Scale by the largest component first, so that squares of tiny entries
-  // (rank-deficient Gram matrices reach 1e-160 and below) cannot underflow.
-  double amax = 0.0;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
-  amax = -block_min(-amax, sh);
-  const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
-  double s = 0.0;
-  for (int r = 1 + threadIdx.x; r < n; r += blockDim.x) {
-    const double vx = x[r].x * sinv, vy = x[r].y * sinv;
-    s = fma(vx, vx, fma(vy, vy, s));
-  }
-  const double xnorm2 = block_sum(s, sh);  // of the scaled column
-  if (threadIdx.x == 0) {
-    const double ar = x[0].x * sinv, ai = -x[0].y * sinv;  // scaled alpha = conj(row[k+1])
-    double beta;
-    double2 tau, scale;
-    if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
-      beta = x[0].x;
-      tau = make_double2(0.0, 0.0);
-      scale = make_double2(0.0, 0.0);
-    } else {
-      const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
-      tau = make_double2((bs - ar) / bs, -ai / bs);
-      const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
-      scale = make_double2(zr / den * sinv, -zi / den * sinv);  // 1 / (alpha - beta)
-      beta = bs * amax;
-    }
-    M.d[k] = row[k].x;
-    M.e[k] = beta;
-    M.tau[k] = tau;
-    scale_sh = scale;
-  }
-  __syncthreads();
-  const double2 sc = scale_sh;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) {
-    x[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(x[r]), sc);
-  }
-}
-
-// p = tau * A22 v, and per-block partial sums of p^+ v.
-__global__ void k_hemv(const __grid_constant__ EigBatch b, int k) {
-  const EigMat& M = b.a[blockIdx.y];
-  const int m = M.m;
-  if (k >= m - 1) return;
-  const int n = m - k - 1;
-  extern __shared__ double2 vs[];
-  const double2* v = M.H + (size_t)k * m + k + 1;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) vs[r] = v[r];
-  __syncthreads();
-  const double2 tau = M.tau[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double2 part = make_double2(0.0, 0.0);
-  for (int r = blockIdx.x * nw + warp; r < n; r += gridDim.x * nw) {
-    const double2* Arow = M.H + (size_t)(k + 1 + r) * m + k + 1;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = lane; c < n; c += 32) acc = cfma(Arow[c], vs[c], acc);
-    acc = warp_sum2(acc);
-    const double2 p = cmul(tau, acc);
-    if (lane == 0) {
-      M.p[r] = p;
-      part = cfma_conj(p, vs[r], part);
-    }
-  }
-  __shared__ double2 sh[32];
-  if (lane == 0) sh[warp] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int w = 0; w < nw; ++w) t = cadd(t, sh[w]);
-    M.part[blockIdx.x] = t;
-  }
-}
-
-// A22 <- A22 - v w^+ - w v^+,  w = p + alpha v,  alpha = -tau (p^+ v) / 2.
-__global__ void k_rank2(const __grid_constant__ EigBatch b, int k, int nparts) {
-  const EigMat& M = b.a[blockIdx.y];
-  const int m = M.m;
-  if (k >= m - 1) return;
-  const int n = m - k - 1;
-  const double2 tau = M.tau[k];
-  double2 dot = make_double2(0.0, 0.0);
-  for (int g = 0; g < nparts; ++g) dot = cadd(dot, M.part[g]);
-  const double2 t2 = cmul(tau, dot);
-  const double2 alpha = make_double2(-0.5 * t2.x, -0.5 * t2.y);
-  const double2* v = M.H + (size_t)k * m + k + 1;
-  const double2* p = M.p;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = blockIdx.x * nw + warp; r < n; r += gridDim.x * nw) {
-    const double2 vr = v[r];
-    const double2 wr = cfma(alpha, vr, p[r]);
-    double2* Arow = M.H + (size_t)(k + 1 + r) * m + k + 1;
-    for (int c = lane; c < n; c += 32) {
-      const double2 vc = v[c];
-      const double2 wc = cfma(alpha, vc, p[c]);
-      double2 a = Arow[c];
-      // a -= vr * conj(wc) + wr * conj(vc)
-      a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
-      a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
-      Arow[c] = a;
-    }
-  }
-}
-
 // ---- bisection --------------------------------------------------------------------
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x, double pivmin) {
-  int cnt = 0;
-  double q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  cnt += (q < 0.0);
+// Number of eigenvalues of T below x: sign changes of the leading principal
+// minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm's theorem), with
+// a zero minor counted as a change.  Division-free: FP64 division is the
+// slowest operation on this part, and the minors are kept in range by exact
+// rescaling with 2^-500 / 2^500.
+__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x) {
+  const double big = 0x1p500, small = 0x1p-500;
+  double pm = 1.0, p = d[0] - x;
+  if (p == 0.0) p = -small;
+  int cnt = (p < 0.0);
   for (int i = 1; i < m; ++i) {
     const double ei = e[i - 1];
-    q = d[i] - x - (ei * ei) / q;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += (q < 0.0);
+    double pn = fma(d[i] - x, p, -(ei * ei) * pm);
+    if (pn == 0.0) pn = (p < 0.0) ? small : -small;
+    cnt += ((pn < 0.0) != (p < 0.0));
+    pm = p;
+    p = pn;
+    const double a = fabs(p);
+    if (a > big) { p *= small; pm *= small; }
+    else if (a < small) { p *= big; pm *= big; }
   }
   return cnt;
 }
@@ -268,7 +154,7 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
     if (hi - lo <= atol) break;
     const double mid = 0.5 * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (sturm_count(M.d, M.e, m, mid, pivmin) > target) hi = mid; else lo = mid;
+    if (sturm_count(M.d, M.e, m, mid) > target) hi = mid; else lo = mid;
   }
   M.evals[j] = 0.5 * (lo + hi);
 }
@@ -451,6 +337,203 @@ __global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ Ei
   }
 }
 
+// ---- persistent Householder reduction ----------------------------------------------------
+// One cooperative launch reduces every matrix of the batch.  Only the upper
+// triangle A[r][c], c >= r, of the trailing matrix is kept current (half the
+// rank-2 work of full storage); row k beyond the diagonal holds v_k.  Per
+// column k: phase V computes p = tau A22 v by strips of 32 columns (each
+// strip reads its columns above the diagonal and its rows right of it, so the
+// product is exact and deterministic without scatter); phase R applies the
+// rank-2 update row by row, and the warp that owns the first trailing row then
+// builds the reflector of column k+1 from that row.  Two grid barriers per column.
+
+constexpr int TD_THREADS = 256;
+constexpr int TD_WARPS = TD_THREADS / 32;
+constexpr int TD_STRIP = 32;
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Grid barrier for a cooperative launch: waits at most ~1 s (2e9 clocks); on
+// timeout it records the failure in st[2] and returns false so every block
+// can leave.  st = {arrival count, generation, error}.
+__device__ bool grid_sync(unsigned int* st) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = st + 1;
+    volatile unsigned int* verr = st + 2;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(st, 1u) == gridDim.x - 1) {
+      atomicExch(st, 0u);
+      __threadfence();
+      atomicAdd(st + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*verr) { ok = 0; break; }
+        if (clock64() - t0 > 2000000000LL) { atomicExch(st + 2, 1u); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_sh = ok && (*verr == 0);
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Reflector of column k from row k (conjugate of the column), by one warp.
+__device__ void house_row(const EigMat& M, int k, int lane) {
+  const int m = M.m;
+  double2* row = M.H + (size_t)k * m;
+  if (k == m - 1) {
+    if (lane == 0) {
+      M.d[k] = row[k].x;
+      M.e[k] = 0.0;
+      M.tau[k] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
+  const int n = m - k - 1;
+  double2* x = row + k + 1;
+  double amax = 0.0;
+  for (int r = lane; r < n; r += 32) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
+  amax = warp_max(amax);
+  const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
+  double s = 0.0;
+  for (int r = 1 + lane; r < n; r += 32) {
+    const double vx = x[r].x * sinv, vy = x[r].y * sinv;
+    s = fma(vx, vx, fma(vy, vy, s));
+  }
+  const double xnorm2 = warp_sum(s);
+  const double ar = x[0].x * sinv, ai = -x[0].y * sinv;
+  double beta;
+  double2 tau, sc;
+  if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
+    beta = x[0].x;
+    tau = make_double2(0.0, 0.0);
+    sc = make_double2(0.0, 0.0);
+  } else {
+    const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
+    tau = make_double2((bs - ar) / bs, -ai / bs);
+    const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
+    sc = make_double2(zr / den * sinv, -zi / den * sinv);
+    beta = bs * amax;
+  }
+  const double dk = row[k].x;
+  __syncwarp();
+  if (lane == 0) {
+    M.d[k] = dk;
+    M.e[k] = beta;
+    M.tau[k] = tau;
+  }
+  for (int r = lane; r < n; r += 32) x[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(x[r]), sc);
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ EigBatch b, int mmax) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * TD_WARPS + warp, nwarps = gridDim.x * TD_WARPS;
+  __shared__ double2 acc_sh[TD_WARPS][TD_STRIP];
+  __shared__ double2 pd_sh[TD_STRIP];
+  for (int i = gw; i < b.n; i += nwarps) house_row(b.a[i], 0, lane);
+  if (!grid_sync(b.bar)) return;
+  for (int k = 0; k < mmax - 1; ++k) {
+    // ---- phase V: p = tau A22 v, one strip of columns per block at a time
+    for (int item = blockIdx.x;; item += gridDim.x) {
+      int rem = item, mi = -1;
+      for (int i = 0; i < b.n; ++i) {
+        const int n = b.a[i].m - k - 1;
+        const int ns = (n > 0) ? (n + TD_STRIP - 1) / TD_STRIP : 0;
+        if (rem < ns) { mi = i; break; }
+        rem -= ns;
+      }
+      if (mi < 0) break;
+      const EigMat& M = b.a[mi];
+      const int m = M.m, n = m - k - 1;
+      const int c0 = rem * TD_STRIP, w = min(TD_STRIP, n - c0);
+      const double2* v = M.H + (size_t)k * m + k + 1;
+      const double2* A = M.H + (size_t)(k + 1) * m + k + 1;
+      const int c = c0 + lane;
+      double2 acc = make_double2(0.0, 0.0);
+      // p[c] = sum_r A[c][r] v[r]: rows r < c through the stored A[r][c] = conj(A[c][r]),
+      // the diagonal as stored, rows r > c (below) through row c itself
+      for (int r = warp; r < c0 + w; r += TD_WARPS) {
+        if (lane < w && c >= r) {
+          const double2 a = A[(size_t)r * m + c];
+          acc = (c == r) ? cfma(a, v[r], acc) : cfma_conj(a, v[r], acc);
+        }
+      }
+      acc_sh[warp][lane] = acc;
+      __syncthreads();
+      const double2 tau = M.tau[k];
+      for (int q = warp; q < w; q += TD_WARPS) {
+        const int cc = c0 + q;
+        double2 a2 = make_double2(0.0, 0.0);
+        for (int r = cc + 1 + lane; r < n; r += 32) a2 = cfma(A[(size_t)cc * m + r], v[r], a2);
+        a2 = warp_sum2(a2);
+        if (lane == 0) {
+          double2 p1 = make_double2(0.0, 0.0);
+          for (int wq = 0; wq < TD_WARPS; ++wq) p1 = cadd(p1, acc_sh[wq][q]);
+          const double2 pc = cmul(tau, cadd(p1, a2));
+          M.p[cc] = pc;
+          pd_sh[q] = cfma_conj(pc, v[cc], make_double2(0.0, 0.0));
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int q = 0; q < w; ++q) t = cadd(t, pd_sh[q]);
+        M.part[rem] = t;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(b.bar)) return;
+    // ---- phase R: A22 -= v w^+ + w v^+ on the upper triangle; reflector of column k+1
+    for (int item = gw;; item += nwarps) {
+      int rem = item, mi = -1;
+      for (int i = 0; i < b.n; ++i) {
+        const int n = b.a[i].m - k - 1;
+        if (n <= 0) continue;
+        if (rem < n) { mi = i; break; }
+        rem -= n;
+      }
+      if (mi < 0) break;
+      const EigMat& M = b.a[mi];
+      const int m = M.m, n = m - k - 1, r = rem;
+      const int ns = (n + TD_STRIP - 1) / TD_STRIP;
+      double2 dot = make_double2(0.0, 0.0);
+      for (int j = 0; j < ns; ++j) dot = cadd(dot, M.part[j]);
+      const double2 t2 = cmul(M.tau[k], dot);
+      const double2 alpha = make_double2(-0.5 * t2.x, -0.5 * t2.y);
+      const double2* v = M.H + (size_t)k * m + k + 1;
+      const double2* p = M.p;
+      const double2 vr = v[r];
+      const double2 wr = cfma(alpha, vr, p[r]);
+      double2* row = M.H + (size_t)(k + 1 + r) * m + k + 1;
+      for (int cc = r + lane; cc < n; cc += 32) {
+        const double2 vc = v[cc];
+        const double2 wc = cfma(alpha, vc, p[cc]);
+        double2 a = row[cc];
+        a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
+        a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
+        row[cc] = a;
+      }
+      if (r == 0) {
+        __syncwarp();
+        house_row(M, k + 1, lane);
+      }
+    }
+    if (!grid_sync(b.bar)) return;
+  }
+}
+
 int max_m(const EigBatch& b) {
   int mm = 0;
   for (int i = 0; i < b.n; ++i) mm = std::max(mm, b.a[i].m);
@@ -469,25 +552,20 @@ int eig_trace(const EigBatch& b, cudaStream_t s) {
 
 int eig_tridiagonalize(const EigBatch& b, cudaStream_t s) {
   if (b.n == 0) return 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_hemv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   const int mm = max_m(b);
-  int launches = 0;
-  for (int k = 0; k < mm; ++k) {
-    k_house<<<b.n, NT, 0, s>>>(b, k);
-    ++launches;
-    const int n = mm - k - 1;
-    if (n <= 0) continue;
-    const int G = std::max(1, std::min({(n + 7) / 8, EIG_PARTS, std::max(1, 1216 / b.n)}));
-    const size_t smem = (size_t)n * sizeof(double2);
-    k_hemv<<<dim3(G, b.n), NT, smem, s>>>(b, k);
-    k_rank2<<<dim3(G, b.n), NT, 0, s>>>(b, k, G);
-    launches += 2;
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TD_THREADS, 0);
+    grid = std::max(1, sms * std::min(per_sm, 2));
   }
-  return launches;
+  int mmax = mm;
+  void* args[] = {const_cast<EigBatch*>(&b), &mmax};
+  if (cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(grid), dim3(TD_THREADS), args, 0, s) != cudaSuccess)
+    return -1;
+  return 1;
 }
 
 int eig_bisect(const EigBatch& b, cudaStream_t s) {

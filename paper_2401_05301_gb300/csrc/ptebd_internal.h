@@ -71,8 +71,8 @@ struct EigMat {
   double* d;         // tridiagonal diagonal [m]
   double* e;         // sub-diagonal [m]
   double2* tau;      // Householder scalars [m]
-  double2* part;     // partial dot products [EIG_PARTS]
-  double2* p;        // hemv result [m]
+  double2* part;     // partial dot products [EIG_PARTS], one per 32-column strip
+  double2* p;        // p = tau A22 v [m]
   double* evals;     // eigenvalues, descending [kmax]
   double* trace;     // [1] trace of H (sum of Re H_rr), taken before reduction
   double* Z;         // m x K real eigenvectors of T (row-major, ld = K)
@@ -86,12 +86,15 @@ struct EigMat {
 struct EigBatch {
   EigMat a[EIG_MAXP];
   int n;
+  unsigned int* bar;  // grid-barrier state {count, generation, error} for the persistent reduction
 };
 
-constexpr int EIG_PARTS = 256;  // max blocks in the hemv stage
+constexpr int EIG_PARTS = 384;  // partial sums of p^+ v, one per strip of 32 columns (m <= 12288)
 
 // Each returns the number of kernel launches issued.
 int eig_trace(const EigBatch& b, cudaStream_t s);
+// One cooperative launch; returns -1 if the launch is refused.  A barrier that
+// times out sets b.bar[2] (checked by the caller after synchronising).
 int eig_tridiagonalize(const EigBatch& b, cudaStream_t s);
 int eig_bisect(const EigBatch& b, cudaStream_t s);
 // Inverse iteration on T for eigenvalues 0..K-1, Newton-Schulz orthonormalisation,
