@@ -155,6 +155,17 @@ const char* tebd_strerror(int status);
 int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
                    int j, double tau, double* out);
 
+/* The complex contraction used by the local update, exposed for direct use and
+ * testing: C = alpha * A * op(B) on device buffers (interleaved complex doubles,
+ * row-major with leading dimensions in complex elements), A: M x K, op(B): K x N
+ * with opB = 0 (B stored K x N) or 1 (B^+, B stored N x K), C: M x N.
+ * precision 0: FP64 on the CUDA cores; 1: split 3xTF32 on the tcgen05 tensor
+ * cores with FP32 accumulation (relative error ~5e-7 of |A||B|).  Enqueued on
+ * cuda_stream (NULL = legacy default stream), not synchronised.  Sizes >= 1,
+ * leading dimensions >= the row lengths; otherwise TEBD_ERR_ARG. */
+int tebd_zgemm(int precision, int opB, int M, int N, int K, double alpha, const double* A, long long lda,
+               const double* B, long long ldb, double* C, long long ldc, void* cuda_stream);
+
 /* Allocation-free nearest-neighbour correlator of one bond.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory when they need the value (a fixed device-memory budget, a

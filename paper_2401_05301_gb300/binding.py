@@ -38,6 +38,8 @@ SIGNATURES = {
     "tebd_profile": (_c_int, [_c_void_p, _c_int, _P_double, _P_ll, _P_double]),
     "tebd_destroy": (None, [_c_void_p]),
     "tebd_strerror": (ctypes.c_char_p, [_c_int]),
+    "tebd_zgemm": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _c_double, _c_void_p, ctypes.c_longlong,
+                            _c_void_p, ctypes.c_longlong, _c_void_p, ctypes.c_longlong, _c_void_p]),
     "tebd_bond_correlator_noalloc": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_int, _c_int, _c_int,
                                              _c_void_p, _c_void_p]),
     "tebd_gate_host": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double, _c_int,

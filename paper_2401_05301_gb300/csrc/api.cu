@@ -458,9 +458,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g1.launch(s, c->precision == 1);
-      c->launches += g2.launch(s, c->precision == 1);
-      c->launches += g3.launch(s, c->precision == 1);
+      c->launches += g1.launch(s, c->precision == 1, c->d_status);
+      c->launches += g2.launch(s, c->precision == 1, c->d_status);
+      c->launches += g3.launch(s, c->precision == 1, c->d_status);
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -521,7 +521,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g6.launch(s, c->precision == 1);
+      c->launches += g6.launch(s, c->precision == 1, c->d_status);
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -565,7 +565,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     for (auto& T : ts) w += 8.0 * (double)T.m2 * T.chi2 * T.n2;
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, w);
-      c->launches += g9.launch(s, c->precision == 1);
+      c->launches += g9.launch(s, c->precision == 1, c->d_status);
     }
     if (int r = check_launch(c)) return r;
   }
@@ -632,6 +632,22 @@ const char* tebd_strerror(int status) {
     case TEBD_ERR_TOO_LARGE: return "size exceeds the fixed scratch capacity";
     default: return "unknown status";
   }
+}
+
+int tebd_zgemm(int precision, int opB, int M, int N, int K, double alpha, const double* A, long long lda,
+               const double* B, long long ldb, double* C, long long ldc, void* cuda_stream) {
+  if ((precision != 0 && precision != 1) || (opB != 0 && opB != 1)) return TEBD_ERR_ARG;
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !is_fin(alpha)) return TEBD_ERR_ARG;
+  if (lda < K || ldc < N || ldb < (opB ? K : N)) return TEBD_ERR_ARG;
+  try {
+    Gemm g(true, OP_N, opB ? OP_C : OP_N);
+    GemmProb& p = g.add(M, N, K, A, lda, B, ldb, C, ldc);
+    p.alpha_re = alpha;
+    g.launch(static_cast<cudaStream_t>(cuda_stream), precision == 1, nullptr);
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return cudaGetLastError() == cudaSuccess ? TEBD_OK : TEBD_ERR_CUDA;
 }
 
 int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c, int j, double tau,

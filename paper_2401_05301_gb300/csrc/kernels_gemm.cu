@@ -185,7 +185,27 @@ int gemm_launch_single(bool complex_, int opA, int opB, const GemmProb& p, cudaS
   return 1;
 }
 
-int Gemm::launch(cudaStream_t s, bool) {
+int Gemm::launch(cudaStream_t s, bool mixed, int* status) {
+  if (mixed && cplx_ && opA_ == OP_N && (opB_ == OP_N || opB_ == OP_C)) {
+    std::vector<TcGemmProb> tp;
+    bool eligible = true;
+    for (const GemmProb& p : probs_) {
+      if (p.s_red || p.s_row || p.s_col || p.accumulate || p.herm || p.alpha_im != 0.0) eligible = false;
+      TcGemmProb q{};
+      q.A = static_cast<const double2*>(p.A);
+      q.B = static_cast<const double2*>(p.B);
+      q.C = static_cast<double2*>(p.C);
+      q.lda = p.lda; q.ldb = p.ldb; q.ldc = p.ldc;
+      q.sA = p.sA; q.sB = p.sB; q.sC = p.sC;
+      q.alpha = p.alpha_re;
+      q.M = p.M; q.N = p.N; q.K = p.K; q.batch = p.batch; q.opB = opB_;
+      tp.push_back(q);
+    }
+    if (eligible) {
+      probs_.clear();
+      return tc_gemm_launch(tp, status, s);
+    }
+  }
   int launches = 0;
   size_t i = 0;
   while (i < probs_.size()) {

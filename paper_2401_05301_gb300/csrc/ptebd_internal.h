@@ -45,13 +45,35 @@ struct GemmBatch {
   int nprob, opA, opB, mixed;
 };
 
+// ---- complex GEMM as split 3xTF32 on tcgen05 tensor cores (kernels_tf32.cu) ------
+// C = alpha * A * op(B), A complex M x K (op N), op(B) in {N, C}; FP64 complex in
+// memory, FP32 accumulation in tensor memory.
+struct TcGemmProb {
+  const double2* A;
+  const double2* B;
+  double2* C;
+  long long lda, ldb, ldc, sA, sB, sC;
+  double alpha;
+  int M, N, K, batch, opB;
+};
+constexpr int TC_MAXP = 24;
+struct TcGemmBatch {
+  TcGemmProb p[TC_MAXP];
+  int tile_start[TC_MAXP + 1];
+  int nprob;
+  int* status;  // set to TEBD_ERR_TIMEOUT if a bounded wait runs out
+};
+int tc_gemm_launch(const std::vector<TcGemmProb>& probs, int* status, cudaStream_t s);
+
 class Gemm {
  public:
   Gemm(bool complex_, int opA, int opB) : cplx_(complex_), opA_(opA), opB_(opB) {}
   GemmProb& add(int M, int N, int K, const void* A, long long lda, const void* B, long long ldb, void* C,
                 long long ldc);
   // Launch everything added so far (in chunks of GEMM_MAXP) on stream; returns launches issued.
-  int launch(cudaStream_t s, bool mixed = false);
+  // mixed: complex problems with op(A) = N, op(B) in {N, C}, real alpha and no
+  // scalings run as split 3xTF32 on the tensor cores instead of FP64.
+  int launch(cudaStream_t s, bool mixed = false, int* status = nullptr);
   size_t size() const { return probs_.size(); }
 
  private:
