@@ -137,6 +137,38 @@ def oracle_sample(n_gates: int, seed_state):
     return time.perf_counter() - t0
 
 
+def served_requests(n: int = 24, rate: float = 8.0):
+    """Seeded Poisson stream shaped like the serving workload, scaled to run in about a
+    minute: 90% chains like the L=64, d=5 mixed-precision one (here L=24, chi_max=32,
+    t = 0.2) and 10% larger d=4 jobs (L=40, chi_max=64, t = 0.4)."""
+    from paper_2401_05301_gb300 import serving
+
+    def make(i, t, rng):
+        if rng.uniform() < 0.9:
+            L = 24
+            return serving.Request(rid=i, arrival=t, L=L, n_max=4, chi_max=32, U=3.0, J=1.0, Jnnn=0.1, K=0.003,
+                                   jc=(L + 1) / 2, dt=0.005, n_steps=40, measure_every=10)
+        L = 40
+        return serving.Request(rid=i, arrival=t, L=L, n_max=3, chi_max=64, U=5.0, J=1.0, Jnnn=0.1, K=0.002,
+                               jc=(L + 1) / 2, dt=0.01, n_steps=40, measure_every=10)
+
+    return serving.poisson_requests(n, rate, workloads.SEED, make)
+
+
+def served_measurement(stream_ptr):
+    """Continuous batching (mixed path) vs one-at-a-time plain FP64 on the same stream."""
+    from paper_2401_05301_gb300 import serving
+    reqs = served_requests()
+    srv = serving.Server(40e9, precision=1, stream_ptr=stream_ptr)
+    batched = serving.latency_stats(srv.run(reqs))
+    fifo_srv = serving.Server(40e9, precision=0, max_active=1, stream_ptr=stream_ptr)
+    fifo = serving.latency_stats(fifo_srv.run(reqs))
+    return {"requests": len(reqs), "arrival_rate_per_s": 8.0,
+            "workload": "Poisson stream: 90% L=24 d=5 chi_max=32 t=0.2, 10% L=40 d=4 chi_max=64 t=0.4",
+            "continuous_batching_mixed": batched, "one_at_a_time_fp64": fifo,
+            "peak_active": srv.peak_active}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -169,6 +201,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="mixed: 3xTF32 tensor-core contractions + FP64 SVD (headline); the FP64 path is timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
     ap.add_argument("--workload", default="trunc_L32", choices=sorted(WORKLOADS),
                     help="trunc_L32 is the measured configuration; parity_L8 is a small case for profiling")
     args = ap.parse_args()
@@ -306,6 +339,10 @@ def main():
                             "fallback 1.9 PFLOP/s bf16 x 1.1/2.25"),
             "note": "algorithmic complex flops 8MNK; the 3xTF32 split issues 3x that on the tensor cores"}
 
+    served = None
+    if not args.no_served and ws == 1:
+        served = served_measurement(stream.cuda_stream)
+
     cpu = None
     if not args.no_cpu_baseline:
         n_cpu = 4
@@ -322,7 +359,7 @@ def main():
             "data": "synthetic", "config": config(args.precision),
             "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
-            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64}
+            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "served": served}
     print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:

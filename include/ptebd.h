@@ -80,6 +80,23 @@ int tebd_init_product(tebd_handle h, const int* occ);
  * the new bond dimensions to size the next launches). */
 int tebd_step(tebd_handle h, int n_steps);
 
+/* Device bytes a handle with these sizes holds once stepped and measured
+ * (state, gates, workspace for min(triples per layer, 24, max_slots > 0 ?
+ * max_slots : 24) concurrent local updates, measurement buffers), written to
+ * *bytes.  Host-only arithmetic: used to admit simulations by an HBM budget
+ * before creating them. */
+int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, double* bytes);
+
+/* Batched form: advance n distinct handles (simulations with any L, n_max,
+ * chi_max and parameters) by n_steps full steps together.  Within every
+ * layer, the triples of all simulations are processed as shared batches: each
+ * stage of the local update is one grouped launch over all of them.  Work
+ * runs on hs[0]'s stream; all handles must be on the same device, hold a
+ * state and use the same "precision" (else TEBD_ERR_ARG).  Each simulation's
+ * result is bitwise the same as stepping it alone.  A device error marks every
+ * member sticky. */
+int tebd_batch_step(tebd_handle* hs, int n, int n_steps);
+
 /* Apply one Trotter layer only: every triple j = residue + 1 (mod 3), 1-based
  * (residue in {0, 1, 2}), with tau = dt/2 (full = 0) or dt (full = 1).  The
  * step counter and t are unchanged.  Used to compare single layers of large

@@ -29,6 +29,8 @@ SIGNATURES = {
     "tebd_init_product": (_c_int, [_c_void_p, _P_int]),
     "tebd_step": (_c_int, [_c_void_p, _c_int]),
     "tebd_layer": (_c_int, [_c_void_p, _c_int, _c_int]),
+    "tebd_batch_step": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, _c_int]),
+    "tebd_estimate_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P_double]),
     "tebd_measure": (_c_int, [_c_void_p, _P_double, _P_double]),
     "tebd_stats": (_c_int, [_c_void_p, _P_double, _P_double, _P_int]),
     "tebd_bond_dims": (_c_int, [_c_void_p, _P_int]),
@@ -78,6 +80,19 @@ def _check(status: int, where: str):
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(_P_double)
+
+
+def estimate_bytes(L, n_max, chi_max, max_slots=0) -> float:
+    """Device bytes a simulation of these sizes will hold (tebd_estimate_bytes)."""
+    out = _c_double()
+    _check(load().tebd_estimate_bytes(L, n_max, chi_max, max_slots, ctypes.byref(out)), "tebd_estimate_bytes")
+    return out.value
+
+
+def batch_step(sims, n_steps: int = 1):
+    """Advance several TEBD handles together (tebd_batch_step)."""
+    arr = (_c_void_p * len(sims))(*[s._h for s in sims])
+    _check(load().tebd_batch_step(arr, len(sims), int(n_steps)), "tebd_batch_step")
 
 
 def gate_host(L, n_max, U, J, Jnnn, K, jc, j, tau) -> np.ndarray:

@@ -16,6 +16,8 @@
 
 using namespace ptebd;
 
+struct tebd_ctx;
+
 namespace {
 
 constexpr int MAX_SLOTS = 24;
@@ -28,6 +30,7 @@ struct Slot {
 };
 
 struct Triple {
+  tebd_ctx* h;  // the simulation this triple belongs to
   int i;        // 0-based first site
   int slot;
   int chl, c1, c2, chr;
@@ -194,20 +197,34 @@ int max_triples_per_layer(int L) {
   return best;
 }
 
+// Device bytes of one workspace slot (one triple in flight) for bond capacity
+// capmax, local dimension d and bond cap chi_max.
+double slot_bytes_for(long long capmax, long long d, long long chi_max) {
+  const long long D = d * d * d, mm = capmax * d, n1max = d * d * capmax;
+  const long long kc = std::min<long long>(mm, chi_max);
+  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 3.0 * mm +
+                 EIG_PARTS + kc * mm) +
+         8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1);
+}
+
+std::vector<int> bond_caps(int L, int d, int chi_max) {
+  std::vector<int> cap(L + 1);
+  for (int k = 0; k <= L; ++k) cap[k] = (int)ipow_cap(d, std::min(k, L - k), chi_max);
+  return cap;
+}
+
 int alloc_workspace(tebd_ctx* c) {
   if (!c->slots.empty()) return TEBD_OK;
-  const long long d = c->d, D = c->D;
+  const long long d = c->d;
   long long capmax = 1;
   for (int v : c->cap) capmax = std::max<long long>(capmax, v);
   c->capmax = capmax;
   c->mmax = capmax * d;
   c->n1max = d * d * capmax;
   c->kcap = std::min<long long>(c->mmax, c->chi_max);
-  if (c->mmax > 12288) return TEBD_ERR_ARG;  // Householder stage stages one column in shared memory
-  const long long mm = c->mmax, kc = c->kcap;
-  const double slot_bytes = 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm +
-                                    capmax * c->n1max + 3.0 * mm + EIG_PARTS + kc * mm) +
-                            8.0 * (4.0 * mm + 3 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1);
+  if (c->mmax > 12288) return TEBD_ERR_ARG;  // the reduction's partial sums are sized for m <= 12288
+  const long long D = c->D, mm = c->mmax, kc = c->kcap;
+  const double slot_bytes = slot_bytes_for(capmax, d, c->chi_max);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
@@ -279,12 +296,14 @@ const double2* gate_ptr(const tebd_ctx* c, int i, int tidx) {
 // Eigen-decomposition of the Gram matrices held in the slots of ts (H, m, kmax
 // already set): trace, tridiagonal reduction, bisection, host choice of K,
 // eigenvectors.  On return the slots' U hold the K leading eigenvectors.
+// c drives the batch (stream, status, pinned buffers); each triple's state,
+// slot and options belong to its owner T.h (several simulations may share a batch).
 int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   EigBatch eb{};
   eb.n = (int)ts.size();
   eb.bar = c->d_bar;
   for (size_t t = 0; t < ts.size(); ++t) {
-    const Slot& S = c->slots[ts[t].slot];
+    const Slot& S = ts[t].h->slots[ts[t].slot];
     EigMat& M = eb.a[t];
     M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p;
     M.evals = S.evals; M.trace = S.scal; M.Z = S.Z; M.Z2 = S.Z2; M.S = S.S; M.work = S.work; M.U = S.U;
@@ -292,7 +311,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     const int n = second ? ts[t].n2 : ts[t].n1;
     // at most min(m, n) singular values are non-zero: noise eigenvalues of a
     // rank-deficient Gram matrix must never widen the bond beyond that
-    M.kmax = (int)std::min<long long>(std::min(M.m, n), c->chi_max);
+    M.kmax = (int)std::min<long long>(std::min(M.m, n), ts[t].h->chi_max);
     M.K = 0;
   }
   {
@@ -314,11 +333,14 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   }
   if (int r = check_launch(c)) return r;
   // read back the eigenvalues and the traces
-  const size_t stride = (size_t)c->kcap + 1;
+  size_t kmax_all = 1;
+  for (int t = 0; t < eb.n; ++t) kmax_all = std::max<size_t>(kmax_all, eb.a[t].kmax);
+  const size_t stride = kmax_all + 1;
+  if (int r = ensure_pinned(c, ts.size() * stride + 8)) return r;
   for (size_t t = 0; t < ts.size(); ++t) {
     const EigMat& M = eb.a[t];
     cudaMemcpyAsync(c->h_pinned + t * stride, M.evals, sizeof(double) * M.kmax, cudaMemcpyDeviceToHost, c->stream);
-    cudaMemcpyAsync(c->h_pinned + t * stride + c->kcap, M.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(c->h_pinned + t * stride + kmax_all, M.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   }
   unsigned int* h_bar = reinterpret_cast<unsigned int*>(c->h_pinned + ts.size() * stride);
   cudaMemcpyAsync(h_bar, c->d_bar + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
@@ -330,7 +352,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   for (size_t t = 0; t < ts.size(); ++t) {
     EigMat& M = eb.a[t];
     const double* ev = c->h_pinned + t * stride;
-    const double trace = c->h_pinned[t * stride + c->kcap];
+    const double trace = c->h_pinned[t * stride + kmax_all];
     if (!is_fin(trace) || !(trace > 0.0)) {
       c->sticky = TEBD_ERR_NONFINITE;
       return TEBD_ERR_NONFINITE;
@@ -339,7 +361,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     // 100x margin for the Gram's rounding), at least one.  Below p ~ 1e-15 the
     // Gram matrix's rounding (~eps_mach * trace) hides the singular values, so
     // no vector is computed there whatever eps_rel says.
-    const double floor_v = std::max(0.01 * c->eps_rel, 1e-15) * trace;
+    const double floor_v = std::max(0.01 * ts[t].h->eps_rel, 1e-15) * trace;
     int K = 0;
     while (K < M.kmax && ev[K] > floor_v) ++K;
     M.K = std::max(1, K);
@@ -374,7 +396,8 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   TruncBatch tb{};
   tb.n = (int)ts.size();
   for (size_t t = 0; t < ts.size(); ++t) {
-    const Slot& S = c->slots[ts[t].slot];
+    const tebd_ctx* o = ts[t].h;
+    const Slot& S = o->slots[ts[t].slot];
     TruncArgs& A = tb.a[t];
     A.Y = S.Th;
     A.K = second ? ts[t].K2 : ts[t].K1;
@@ -382,14 +405,14 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     A.trace = S.scal;
     A.s_sorted = S.s_sorted;
     A.perm = S.perm;
-    A.lam_out = c->lam[ts[t].i + (second ? 2 : 1)];
+    A.lam_out = o->lam[ts[t].i + (second ? 2 : 1)];
     A.chi_out = S.chi;
     A.norm_out = S.scal + 1;
     A.w_out = S.scal + 2;
     A.w_total = nullptr;
-    A.chi_max = std::min(c->chi_max, c->cap[ts[t].i + (second ? 2 : 1)]);
-    A.w_cut = c->w_cut;
-    A.eps_rel = c->eps_rel;
+    A.chi_max = std::min(o->chi_max, o->cap[ts[t].i + (second ? 2 : 1)]);
+    A.w_cut = o->w_cut;
+    A.eps_rel = o->eps_rel;
     A.status = c->d_status;
   }
   {
@@ -399,8 +422,9 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   // chi_max above is also the bond capacity, so chi' can never overrun lam or B
   if (int r = check_launch(c)) return r;
   const size_t stride = 4;
+  if (int r = ensure_pinned(c, ts.size() * stride + 8)) return r;
   for (size_t t = 0; t < ts.size(); ++t) {
-    const Slot& S = c->slots[ts[t].slot];
+    const Slot& S = ts[t].h->slots[ts[t].slot];
     cudaMemcpyAsync(c->h_pinned + t * stride, S.scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(reinterpret_cast<int*>(c->h_pinned + t * stride + 2), S.chi, sizeof(int), cudaMemcpyDeviceToHost,
                     c->stream);
@@ -415,7 +439,7 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   for (size_t t = 0; t < ts.size(); ++t) {
     const double* h = c->h_pinned + t * stride;
     const int chi = *reinterpret_cast<const int*>(h + 2);
-    if (chi < 1 || chi > c->cap[ts[t].i + (second ? 2 : 1)]) {
+    if (chi < 1 || chi > ts[t].h->cap[ts[t].i + (second ? 2 : 1)]) {
       c->sticky = TEBD_ERR_STATE;
       return TEBD_ERR_STATE;
     }
@@ -425,42 +449,48 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   return TEBD_OK;
 }
 
-// One batch of independent local updates (disjoint triples), FP64 path.
+// One batch of independent local updates (disjoint triples, possibly of
+// different simulations), driven on c's stream.  c->precision selects the
+// contraction path for the whole batch.
 int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
-  const int d = c->d, D = c->D;
   cudaStream_t s = c->stream;
+  const bool mixed = c->precision == 1;
   for (auto& T : ts) {
-    T.chl = c->chi[T.i]; T.c1 = c->chi[T.i + 1]; T.c2 = c->chi[T.i + 2]; T.chr = c->chi[T.i + 3];
-    T.m1 = T.chl * d;
-    T.n1 = d * d * T.chr;
+    const tebd_ctx* o = T.h;
+    T.chl = o->chi[T.i]; T.c1 = o->chi[T.i + 1]; T.c2 = o->chi[T.i + 2]; T.chr = o->chi[T.i + 3];
+    T.m1 = T.chl * o->d;
+    T.n1 = o->d * o->d * T.chr;
   }
   // theta~ = B_i B_{i+1} B_{i+2}; C = G theta~; Gram H1 = (lam C)(lam C)^+
   {
     Gemm g1(true, OP_N, OP_N), g2(true, OP_N, OP_N), g3(true, OP_N, OP_N), g4(true, OP_N, OP_C);
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
-      g1.add(T.chl * d, d * T.c2, T.c1, c->B[T.i], T.c1, c->B[T.i + 1], (long long)d * T.c2, S.X, (long long)d * T.c2);
-      g2.add(T.chl * d * d, d * T.chr, T.c2, S.X, T.c2, c->B[T.i + 2], (long long)d * T.chr, S.Th, (long long)d * T.chr);
-      GemmProb& p3 = g3.add(D, T.chr, D, gate_ptr(c, T.i, tidx), D, S.Th, T.chr, S.Cb, T.chr);
+      tebd_ctx* o = T.h;
+      const int d = o->d, D = o->D;
+      const Slot& S = o->slots[T.slot];
+      g1.add(T.chl * d, d * T.c2, T.c1, o->B[T.i], T.c1, o->B[T.i + 1], (long long)d * T.c2, S.X, (long long)d * T.c2);
+      g2.add(T.chl * d * d, d * T.chr, T.c2, S.X, T.c2, o->B[T.i + 2], (long long)d * T.chr, S.Th, (long long)d * T.chr);
+      GemmProb& p3 = g3.add(D, T.chr, D, gate_ptr(o, T.i, tidx), D, S.Th, T.chr, S.Cb, T.chr);
       p3.batch = T.chl;
       p3.sA = 0;
       p3.sB = p3.sC = (long long)D * T.chr;
       GemmProb& p4 = g4.add(T.m1, T.m1, T.n1, S.Cb, T.n1, S.Cb, T.n1, S.H, T.m1);
-      p4.s_row = p4.s_col = c->lam[T.i];
+      p4.s_row = p4.s_col = o->lam[T.i];
       p4.row_div = p4.col_div = d;
       p4.herm = 1;
     }
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
+      const double d = T.h->d, D = T.h->D;
       wc += 8.0 * ((double)T.chl * d * d * T.c2 * T.c1 + (double)T.chl * d * d * d * T.chr * T.c2 +
-                   (double)D * D * T.chr * T.chl);
+                   D * D * T.chr * T.chl);
       wg += 4.0 * (double)T.m1 * T.m1 * T.n1;
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g1.launch(s, c->precision == 1, c->d_status);
-      c->launches += g2.launch(s, c->precision == 1, c->d_status);
-      c->launches += g3.launch(s, c->precision == 1, c->d_status);
+      c->launches += g1.launch(s, mixed, c->d_status);
+      c->launches += g2.launch(s, mixed, c->d_status);
+      c->launches += g3.launch(s, mixed, c->d_status);
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -468,7 +498,8 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     if (int r = check_launch(c)) return r;
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
+      const Slot& S = T.h->slots[T.slot];
+      const int d = T.h->d;
       debug_dump(c, "X", T.i, S.X, 2ull * T.chl * d * d * T.c2);
       debug_dump(c, "Theta", T.i, S.Th, 2ull * T.m1 * T.n1);
       debug_dump(c, "C", T.i, S.Cb, 2ull * T.m1 * T.n1);
@@ -479,22 +510,22 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   {  // Y1 = U1^+ (lam C)
     Gemm g5(true, OP_CJ, OP_N);
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
+      const Slot& S = T.h->slots[T.slot];
       GemmProb& p = g5.add(T.K1, T.n1, T.m1, S.U, T.m1, S.Cb, T.n1, S.Th, T.n1);
-      p.s_red = c->lam[T.i];
-      p.red_div = d;
+      p.s_red = T.h->lam[T.i];
+      p.red_div = T.h->d;
     }
     double w = 0.0;
     for (auto& T : ts) w += 8.0 * (double)T.K1 * T.n1 * T.m1;
     ProfScope ps(c, TEBD_PROF_PROJECT, w);
     c->launches += g5.launch(s);
   }
-  for (auto& T : ts) debug_dump(c, "Y1", T.i, c->slots[T.slot].Th, 2ull * T.K1 * T.n1);
+  for (auto& T : ts) debug_dump(c, "Y1", T.i, T.h->slots[T.slot].Th, 2ull * T.K1 * T.n1);
   if (int r = truncate_stage(c, ts, false)) return r;
   {
     std::vector<GatherArgs> ga;
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
+      const Slot& S = T.h->slots[T.slot];
       ga.push_back(GatherArgs{S.Th, S.perm, S.s_sorted, S.V1h, T.chi1, T.n1});
     }
     {
@@ -504,13 +535,15 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     // B_i = C V1 / ||s||;  Gram H2 = (lam' V1^+)(lam' V1^+)^+ viewed as (chi' d) x (d chr)
     Gemm g6(true, OP_N, OP_C), g7(true, OP_N, OP_C);
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
+      tebd_ctx* o = T.h;
+      const int d = o->d;
+      const Slot& S = o->slots[T.slot];
       T.m2 = T.chi1 * d;
       T.n2 = d * T.chr;
-      GemmProb& p6 = g6.add(T.m1, T.chi1, T.n1, S.Cb, T.n1, S.V1h, T.n1, c->B[T.i], T.chi1);
+      GemmProb& p6 = g6.add(T.m1, T.chi1, T.n1, S.Cb, T.n1, S.V1h, T.n1, o->B[T.i], T.chi1);
       p6.alpha_re = 1.0 / T.norm1;
       GemmProb& p7 = g7.add(T.m2, T.m2, T.n2, S.V1h, T.n2, S.V1h, T.n2, S.H, T.m2);
-      p7.s_row = p7.s_col = c->lam[T.i + 1];
+      p7.s_row = p7.s_col = o->lam[T.i + 1];
       p7.row_div = p7.col_div = d;
       p7.herm = 1;
     }
@@ -521,7 +554,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g6.launch(s, c->precision == 1, c->d_status);
+      c->launches += g6.launch(s, mixed, c->d_status);
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -533,10 +566,10 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   {  // Y2 = U2^+ (lam' V1^+)
     Gemm g8(true, OP_CJ, OP_N);
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
+      const Slot& S = T.h->slots[T.slot];
       GemmProb& p = g8.add(T.K2, T.n2, T.m2, S.U, T.m2, S.V1h, T.n2, S.Th, T.n2);
-      p.s_red = c->lam[T.i + 1];
-      p.red_div = d;
+      p.s_red = T.h->lam[T.i + 1];
+      p.red_div = T.h->d;
     }
     double w = 0.0;
     for (auto& T : ts) w += 8.0 * (double)T.K2 * T.n2 * T.m2;
@@ -547,8 +580,8 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   {
     std::vector<GatherArgs> ga;
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
-      ga.push_back(GatherArgs{S.Th, S.perm, S.s_sorted, c->B[T.i + 2], T.chi2, T.n2});
+      const Slot& S = T.h->slots[T.slot];
+      ga.push_back(GatherArgs{S.Th, S.perm, S.s_sorted, T.h->B[T.i + 2], T.chi2, T.n2});
     }
     {
       ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
@@ -557,43 +590,63 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     // B_{i+1} = V1^+ V2 / ||s2||,  B_{i+2} = V2^+ (gathered above)
     Gemm g9(true, OP_N, OP_C);
     for (auto& T : ts) {
-      const Slot& S = c->slots[T.slot];
-      GemmProb& p = g9.add(T.m2, T.chi2, T.n2, S.V1h, T.n2, c->B[T.i + 2], T.n2, c->B[T.i + 1], T.chi2);
+      tebd_ctx* o = T.h;
+      const Slot& S = o->slots[T.slot];
+      GemmProb& p = g9.add(T.m2, T.chi2, T.n2, S.V1h, T.n2, o->B[T.i + 2], T.n2, o->B[T.i + 1], T.chi2);
       p.alpha_re = 1.0 / T.norm2;
     }
     double w = 0.0;
     for (auto& T : ts) w += 8.0 * (double)T.m2 * T.chi2 * T.n2;
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, w);
-      c->launches += g9.launch(s, c->precision == 1, c->d_status);
+      c->launches += g9.launch(s, mixed, c->d_status);
     }
     if (int r = check_launch(c)) return r;
   }
   for (auto& T : ts) {
-    c->chi[T.i + 1] = T.chi1;
-    c->chi[T.i + 2] = T.chi2;
-    c->w_total += T.w1 + T.w2;
-    c->gate_updates += 1;
+    T.h->chi[T.i + 1] = T.chi1;
+    T.h->chi[T.i + 2] = T.chi2;
+    T.h->w_total += T.w1 + T.w2;
+    T.h->gate_updates += 1;
   }
   return TEBD_OK;
 }
 
-int run_layer(tebd_ctx* c, int residue, int tidx) {
-  std::vector<int> starts;
-  for (int i = residue; i + 2 < c->L; i += 3) starts.push_back(i);
-  const int ns = (int)c->slots.size();
-  for (size_t k0 = 0; k0 < starts.size(); k0 += ns) {
+// One Trotter layer (triples i = residue mod 3, time index tidx) of every
+// simulation in hs, as chunks of at most EIG_MAXP triples in which each
+// simulation uses at most its own number of workspace slots.  c drives.
+int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, int tidx) {
+  struct Pending { tebd_ctx* h; int i; };
+  std::vector<Pending> all;
+  for (tebd_ctx* h : hs)
+    for (int i = residue; i + 2 < h->L; i += 3) all.push_back({h, i});
+  size_t next = 0;
+  while (next < all.size()) {
     std::vector<Triple> ts;
-    for (size_t k = k0; k < std::min(starts.size(), k0 + ns); ++k) {
+    std::vector<std::pair<tebd_ctx*, int>> used;  // slots taken per simulation in this chunk
+    while (next < all.size() && (int)ts.size() < EIG_MAXP) {
+      tebd_ctx* h = all[next].h;
+      int k = 0;
+      for (auto& u : used)
+        if (u.first == h) k = u.second;
+      if (k >= (int)h->slots.size()) break;  // this simulation's slots are full: close the chunk
       Triple T{};
-      T.i = starts[k];
-      T.slot = (int)(k - k0);
+      T.h = h;
+      T.i = all[next].i;
+      T.slot = k;
       ts.push_back(T);
+      bool found = false;
+      for (auto& u : used)
+        if (u.first == h) { ++u.second; found = true; }
+      if (!found) used.push_back({h, 1});
+      ++next;
     }
     if (int r = update_chunk(c, ts, tidx)) return r;
   }
   return TEBD_OK;
 }
+
+int run_layer(tebd_ctx* c, int residue, int tidx) { return run_layer_multi(c, {c}, residue, tidx); }
 
 int ensure_measure_ws(tebd_ctx* c) {
   if (c->mN) return TEBD_OK;
@@ -685,8 +738,7 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
     return TEBD_ERR_CUDA;
   }
   try {
-    c->cap.resize(L + 1);
-    for (int k = 0; k <= L; ++k) c->cap[k] = (int)ipow_cap(c->d, std::min(k, L - k), chi_max);
+    c->cap = bond_caps(L, c->d, chi_max);
     c->chi.assign(L + 1, 1);
     c->B.resize(L);
     c->lam.resize(L + 1);
@@ -832,6 +884,57 @@ int tebd_step(tebd_handle h, int n_steps) {
     return TEBD_ERR_OOM;
   }
   return TEBD_OK;
+}
+
+int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, double* bytes) {
+  if (!bytes || L < 3 || n_max < 1 || n_max > 7 || chi_max < 1 || max_slots < 0) return TEBD_ERR_ARG;
+  const int d = n_max + 1, D = d * d * d;
+  const std::vector<int> cap = bond_caps(L, d, chi_max);
+  double b = 0.0;
+  long long capmax = 1;
+  for (int k = 0; k < L; ++k) b += 16.0 * cap[k] * d * cap[k + 1];
+  for (int k = 0; k <= L; ++k) {
+    b += 8.0 * cap[k];
+    capmax = std::max<long long>(capmax, cap[k]);
+  }
+  b += 16.0 * 2.0 * (L - 2) * (double)D * D;  // gates
+  int slots = std::min(max_triples_per_layer(L), MAX_SLOTS);
+  if (max_slots > 0) slots = std::min(slots, max_slots);
+  b += slots * slot_bytes_for(capmax, d, chi_max);
+  b += 16.0 * MEAS_CHUNK * (2.0 * capmax * d * capmax + 2.0 * capmax * capmax) + 24.0 * L;  // measurement
+  *bytes = b;
+  return TEBD_OK;
+}
+
+int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
+  if (!hs || n < 1 || n_steps < 0) return TEBD_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return TEBD_ERR_ARG;
+    if (hs[i]->sticky != TEBD_OK) return hs[i]->sticky;
+    if (!hs[i]->have_state) return TEBD_ERR_STATE;
+    if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision) return TEBD_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return TEBD_ERR_ARG;
+  }
+  if (n_steps == 0) return TEBD_OK;
+  tebd_ctx* c = hs[0];
+  std::vector<tebd_ctx*> v(hs, hs + n);
+  int r = TEBD_OK;
+  try {
+    for (tebd_ctx* h : v)
+      if ((r = alloc_workspace(h)) != TEBD_OK) return r;
+    const int sched[5][2] = {{0, 0}, {1, 0}, {2, 1}, {1, 0}, {0, 0}};
+    for (int step = 0; step < n_steps && r == TEBD_OK; ++step) {
+      for (int l = 0; l < 5 && r == TEBD_OK; ++l) r = run_layer_multi(c, v, sched[l][0], sched[l][1]);
+      if (r == TEBD_OK)
+        for (tebd_ctx* h : v) h->steps += 1;
+    }
+  } catch (...) {
+    r = TEBD_ERR_OOM;
+  }
+  if (r != TEBD_OK && c->sticky != TEBD_OK)  // a device error on the shared stream affects every member
+    for (tebd_ctx* h : v) h->sticky = c->sticky;
+  return r;
 }
 
 int tebd_layer(tebd_handle h, int residue, int full) {

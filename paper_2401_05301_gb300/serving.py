@@ -1,0 +1,183 @@
+"""Continuous-batching request loop for TEBD simulations (host-side scheduling).
+
+Requests (a chain, its Hamiltonian parameters, chi_max, dt, number of steps
+and measurement interval) arrive over time.  The loop
+
+* admits a waiting request as soon as its device footprint
+  (``tebd_estimate_bytes``) fits in the HBM budget and a slot is free,
+* keeps every admitted simulation's MPS resident on the GPU,
+* advances all admitted simulations together, one second-order step per
+  iteration, with ``tebd_batch_step`` (each stage of every layer is one
+  grouped launch over the triples of all of them, so newly admitted requests
+  share the device with those already running),
+* streams n_j and currents back at each request's measurement interval, and
+* retires finished simulations, freeing their memory for the next admissions.
+
+Each result is bitwise the same as running the request alone (the batched
+kernels treat every triple independently); ``tests/test_gpu_serving.py``
+checks this.  Latency = completion time - arrival time.
+"""
+from __future__ import annotations
+
+import heapq
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+from . import binding
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float               # seconds after the loop starts
+    L: int
+    n_max: int
+    chi_max: int
+    U: float
+    J: float
+    Jnnn: float
+    K: float
+    jc: float
+    dt: float
+    n_steps: int
+    measure_every: int = 10
+    occ: Optional[np.ndarray] = None
+    w_cut: float = 0.0
+    eps_rel: float = 1e-12
+    max_slots: int = 0
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float = 0.0
+    finished: float = 0.0
+    times: list = field(default_factory=list)
+    densities: list = field(default_factory=list)
+    currents: list = field(default_factory=list)
+    gate_updates: int = 0
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class _Active:
+    def __init__(self, req: Request, sim: binding.TEBD, nbytes: float, res: Result):
+        self.req, self.sim, self.nbytes, self.res = req, sim, nbytes, res
+        self.done_steps = 0
+
+
+class Server:
+    """HBM-budgeted continuous batching of TEBD simulations on one GPU."""
+
+    def __init__(self, hbm_budget_bytes: float, precision: int = 1, max_active: int = 64,
+                 stream_ptr: Optional[int] = None, on_observables: Optional[Callable] = None,
+                 clock: Callable[[], float] = time.perf_counter, sim_factory: Callable = None,
+                 step_fn: Callable = None, estimate_fn: Callable = None):
+        self.budget = float(hbm_budget_bytes)
+        self.precision = int(precision)
+        self.max_active = int(max_active)
+        self.stream_ptr = stream_ptr
+        self.on_observables = on_observables
+        self.clock = clock
+        self.sim_factory = sim_factory or binding.TEBD
+        self.step_fn = step_fn or binding.batch_step
+        self.estimate_fn = estimate_fn or binding.estimate_bytes
+        self.peak_used = 0.0
+        self.peak_active = 0
+
+    def footprint(self, req: Request) -> float:
+        return self.estimate_fn(req.L, req.n_max, req.chi_max, req.max_slots)
+
+    def _admit(self, req: Request, now: float) -> _Active:
+        sim = self.sim_factory(req.L, req.n_max, req.chi_max, req.U, req.J, req.Jnnn, req.K, req.jc, req.dt,
+                               w_cut=req.w_cut, eps_rel=req.eps_rel, precision=self.precision,
+                               stream=self.stream_ptr)
+        if req.max_slots:
+            sim.set_option("max_slots", req.max_slots)
+        occ = req.occ if req.occ is not None else np.array([1 if j % 2 == 1 else 0 for j in range(1, req.L + 1)])
+        sim.init_product(occ)
+        return _Active(req, sim, self.footprint(req), Result(req.rid, req.arrival, admitted=now))
+
+    def run(self, requests) -> dict:
+        """Serve every request; returns {rid: Result} once all have finished."""
+        pending = [(r.arrival, r.rid, r) for r in requests]
+        heapq.heapify(pending)
+        for r in requests:
+            if self.footprint(r) > self.budget:
+                raise ValueError(f"request {r.rid} needs more than the whole HBM budget")
+        active: list[_Active] = []
+        results: dict[int, Result] = {}
+        used = 0.0
+        t0 = self.clock()
+        while pending or active:
+            now = self.clock() - t0
+            # admit in arrival order while the budget and the slot count allow
+            while pending and pending[0][0] <= now and len(active) < self.max_active:
+                req = pending[0][2]
+                need = self.footprint(req)
+                if used + need > self.budget:
+                    break
+                heapq.heappop(pending)
+                active.append(self._admit(req, now))
+                used += need
+                self.peak_used = max(self.peak_used, used)
+                self.peak_active = max(self.peak_active, len(active))
+            if not active:
+                if pending:  # idle until the next arrival
+                    time.sleep(max(0.0, min(0.01, pending[0][0] - now)))
+                continue
+            self.step_fn([a.sim for a in active], 1)
+            now = self.clock() - t0
+            still = []
+            for a in active:
+                a.done_steps += 1
+                if a.done_steps % a.req.measure_every == 0 or a.done_steps == a.req.n_steps:
+                    n, cur = a.sim.measure()
+                    a.res.times.append(a.done_steps * a.req.dt)
+                    a.res.densities.append(n)
+                    a.res.currents.append(cur)
+                    if self.on_observables:
+                        self.on_observables(a.req.rid, a.done_steps * a.req.dt, n, cur)
+                if a.done_steps >= a.req.n_steps:
+                    a.res.finished = self.clock() - t0
+                    a.res.gate_updates = a.sim.counters()[0]
+                    results[a.req.rid] = a.res
+                    a.sim.close()
+                    used -= a.nbytes
+                else:
+                    still.append(a)
+            active = still
+        return results
+
+
+def run_alone(req: Request, precision: int = 1, stream_ptr: Optional[int] = None) -> Result:
+    """The same request on its own handle, stepped alone (reference for the mix)."""
+    srv = Server(float("inf"), precision=precision, stream_ptr=stream_ptr)
+    r = Request(**{**req.__dict__, "arrival": 0.0})
+    return srv.run([r])[req.rid]
+
+
+def latency_stats(results: dict) -> dict:
+    lat = np.array([r.latency for r in results.values()])
+    gates = sum(r.gate_updates for r in results.values())
+    span = max(r.finished for r in results.values()) - min(r.arrival for r in results.values())
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "requests": len(lat), "gate_updates": int(gates),
+            "throughput_gate_updates_per_s": gates / span if span > 0 else None, "span_s": span}
+
+
+def poisson_requests(n: int, rate_per_s: float, seed: int, make: Callable[[int, float, np.random.Generator], Request]):
+    """n requests with exponential inter-arrival times (seeded); make(i, t, rng) builds each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        out.append(make(i, t, rng))
+    return out
