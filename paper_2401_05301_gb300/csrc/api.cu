@@ -24,7 +24,7 @@ constexpr int MAX_SLOTS = 24;
 constexpr int MEAS_CHUNK = GEMM_MAXP;
 
 struct Slot {
-  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *U;
+  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *pp, *U;
   double *d, *e, *evals, *Z, *Z2, *S, *work, *s_sorted, *scal;  // scal: [0] trace [1] norm [2] w
   int *perm, *chi;
 };
@@ -202,7 +202,7 @@ int max_triples_per_layer(int L) {
 double slot_bytes_for(long long capmax, long long d, long long chi_max) {
   const long long D = d * d * d, mm = capmax * d, n1max = d * d * capmax;
   const long long kc = std::min<long long>(mm, chi_max);
-  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 3.0 * mm +
+  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 4.0 * mm +
                  EIG_PARTS + kc * mm) +
          8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1);
 }
@@ -241,6 +241,7 @@ int alloc_workspace(tebd_ctx* c) {
     S.tau = dalloc<double2>(c, mm);
     S.part = dalloc<double2>(c, EIG_PARTS);
     S.p = dalloc<double2>(c, mm);
+    S.pp = dalloc<double2>(c, mm);
     S.U = dalloc<double2>(c, kc * mm);
     S.d = dalloc<double>(c, mm);
     S.e = dalloc<double>(c, mm);
@@ -253,7 +254,7 @@ int alloc_workspace(tebd_ctx* c) {
     S.scal = dalloc<double>(c, 4);
     S.perm = dalloc<int>(c, mm);
     S.chi = dalloc<int>(c, 1);
-    if (!S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
+    if (!S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.pp || !S.U || !S.d || !S.e ||
         !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
       if (s == 0) return TEBD_ERR_OOM;
       break;
@@ -305,7 +306,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   for (size_t t = 0; t < ts.size(); ++t) {
     const Slot& S = ts[t].h->slots[ts[t].slot];
     EigMat& M = eb.a[t];
-    M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p;
+    M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p; M.pp = S.pp;
     M.evals = S.evals; M.trace = S.scal; M.Z = S.Z; M.Z2 = S.Z2; M.S = S.S; M.work = S.work; M.U = S.U;
     M.m = second ? ts[t].m2 : ts[t].m1;
     const int n = second ? ts[t].n2 : ts[t].n1;

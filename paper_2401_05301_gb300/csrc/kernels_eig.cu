@@ -135,28 +135,35 @@ __device__ void gershgorin(const double* d, const double* e, int m, double* sh, 
   gu = -block_min(hi, sh);
 }
 
+// Multisection: one warp per eigenvalue; each iteration the 32 lanes count
+// the eigenvalues below 32 interior points of the current interval, which
+// shrinks it 33-fold (about 11 iterations to machine precision instead of 52).
 __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   const EigMat& M = b.a[blockIdx.y];
   const int m = M.m;
   __shared__ double sh[33];
   double gl, gu;
   gershgorin(M.d, M.e, m, sh, gl, gu);
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (j >= M.kmax || j >= m) return;
   const double bnorm = fmax(fabs(gl), fabs(gu));
-  const double pivmin = DBL_MIN * fmax(1.0, bnorm * bnorm);
-  const double eps = DBL_EPSILON;
-  double lo = gl - 2.0 * eps * bnorm * m - 4.0 * pivmin;
-  double hi = gu + 2.0 * eps * bnorm * m + 4.0 * pivmin;
-  const double atol = 2.0 * eps * bnorm + 4.0 * pivmin;
+  const double eps = DBL_EPSILON, tiny = DBL_MIN * fmax(1.0, bnorm * bnorm);
+  double lo = gl - 2.0 * eps * bnorm * m - 4.0 * tiny;
+  double hi = gu + 2.0 * eps * bnorm * m + 4.0 * tiny;
+  const double atol = 2.0 * eps * bnorm + 4.0 * tiny;
   const int target = m - 1 - j;  // ascending index of the j-th largest
-  for (int it = 0; it < 200; ++it) {
-    if (hi - lo <= atol) break;
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(M.d, M.e, m, mid) > target) hi = mid; else lo = mid;
+  for (int it = 0; it < 40 && hi - lo > atol; ++it) {
+    const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
+    const bool above = sturm_count(M.d, M.e, m, x) > target;  // eigenvalue lies below x
+    const unsigned ball = __ballot_sync(0xffffffffu, above);
+    const int l0 = ball ? (__ffs(ball) - 1) : 32;  // first point above the eigenvalue (32: none)
+    const double xa = __shfl_sync(0xffffffffu, x, l0 > 0 ? l0 - 1 : 0);
+    const double xb = __shfl_sync(0xffffffffu, x, l0 < 32 ? l0 : 31);
+    if (l0 > 0) lo = xa;
+    if (l0 < 32) hi = xb;
   }
-  M.evals[j] = 0.5 * (lo + hi);
+  if (lane == 0) M.evals[j] = 0.5 * (lo + hi);
 }
 
 // ---- inverse iteration ----------------------------------------------------------------
@@ -304,34 +311,54 @@ __global__ void k_z_to_u(const __grid_constant__ EigBatch b, int use_z2) {
   }
 }
 
-constexpr int CPB = 2;  // eigenvectors per block in the back-transformation
+constexpr int CPB = 8;  // eigenvectors per block in the back-transformation
 
+// U <- H(0) H(1) ... H(m-2) U, one block per CPB eigenvectors; per reflector the
+// CPB dot products v^+ u are reduced together (one round of barriers).
 __global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ EigBatch b) {
   const EigMat& M = b.a[blockIdx.y];
   const int m = M.m, K = M.K;
   const int c0 = blockIdx.x * CPB;
   if (c0 >= K) return;
   const int ncol = min(CPB, K - c0);
-  __shared__ double sh[33];
+  __shared__ double2 red[NT / 32][CPB];
+  __shared__ double2 wsh[CPB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = m - 2; k >= 0; --k) {
     const double2 tau = M.tau[k];
     if (tau.x == 0.0 && tau.y == 0.0) continue;
     const int n = m - k - 1;
     const double2* v = M.H + (size_t)k * m + k + 1;
-    double2 w[CPB];
-    for (int cc = 0; cc < CPB; ++cc) {
-      double2 acc = make_double2(0.0, 0.0);
-      if (cc < ncol) {
-        const double2* u = M.U + (size_t)(c0 + cc) * m + k + 1;
-        for (int r = threadIdx.x; r < n; r += blockDim.x) acc = cfma_conj(v[r], u[r], acc);
-      }
-      acc.x = block_sum(acc.x, sh);
-      acc.y = block_sum(acc.y, sh);
-      w[cc] = cmul(tau, acc);
+    double2 acc[CPB];
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) acc[cc] = make_double2(0.0, 0.0);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 vr = v[r];
+#pragma unroll
+      for (int cc = 0; cc < CPB; ++cc)
+        if (cc < ncol) acc[cc] = cfma_conj(vr, M.U[(size_t)(c0 + cc) * m + k + 1 + r], acc[cc]);
     }
-    for (int cc = 0; cc < ncol; ++cc) {
-      double2* u = M.U + (size_t)(c0 + cc) * m + k + 1;
-      for (int r = threadIdx.x; r < n; r += blockDim.x) u[r] = csub(u[r], cmul(v[r], w[cc]));
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) {
+      const double2 t = warp_sum2(acc[cc]);
+      if (lane == 0) red[warp][cc] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < CPB) {
+      double2 t = make_double2(0.0, 0.0);
+      for (int w = 0; w < NT / 32; ++w) t = cadd(t, red[w][threadIdx.x]);
+      wsh[threadIdx.x] = cmul(tau, t);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 vr = v[r];
+#pragma unroll
+      for (int cc = 0; cc < CPB; ++cc) {
+        if (cc < ncol) {
+          double2* u = M.U + (size_t)(c0 + cc) * m + k + 1 + r;
+          *u = csub(*u, cmul(vr, wsh[cc]));
+        }
+      }
     }
     __syncthreads();
   }
@@ -341,45 +368,42 @@ __global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ Ei
 // One cooperative launch reduces every matrix of the batch.  Only the upper
 // triangle A[r][c], c >= r, of the trailing matrix is kept current (half the
 // rank-2 work of full storage); row k beyond the diagonal holds v_k.  Per
-// column k: phase V computes p = tau A22 v by strips of 32 columns (each
-// strip reads its columns above the diagonal and its rows right of it, so the
-// product is exact and deterministic without scatter); phase R applies the
-// rank-2 update row by row, and the warp that owns the first trailing row then
-// builds the reflector of column k+1 from that row.  Two grid barriers per column.
+// column k: phase V computes p = tau A22 v by strips of 32 columns (each strip
+// reads its columns above the diagonal and its rows right of it, so the
+// product is exact and deterministic without scatter), phase W forms
+// w = p + alpha v once per element, and phase R applies the rank-2 update row
+// by row; the block that owns the first trailing row then builds the reflector
+// of column k+1 from it.  Every FP64 operation is scarce on this part, so sums
+// stay in registers and no per-element quantity is recomputed.  Three grid
+// barriers per column.
 
 constexpr int TD_THREADS = 256;
 constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
 
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return __shfl_sync(0xffffffffu, v, 0);
-}
 
-// Grid barrier for a cooperative launch: waits at most ~1 s (2e9 clocks); on
-// timeout it records the failure in st[2] and returns false so every block
-// can leave.  st = {arrival count, generation, error}.
-__device__ bool grid_sync(unsigned int* st) {
+// Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
+// Every block adds 1 to the count with a fire-and-forget release reduction
+// (no serialised round trips) and polls it with acquire loads until it reaches
+// the next multiple of the grid size (`target`, advanced by each call).  Waits
+// at most ~1 s (2e9 clocks); on timeout it records the failure in st[2] and
+// returns false so every block can leave.  The count starts at 0 per launch.
+__device__ bool grid_sync(unsigned int* st, unsigned int& target) {
   __shared__ int ok_sh;
   __syncthreads();
+  target += gridDim.x;
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = st + 1;
     volatile unsigned int* verr = st + 2;
-    const unsigned int g = *vgen;
-    __threadfence();
     int ok = 1;
-    if (atomicAdd(st, 1u) == gridDim.x - 1) {
-      atomicExch(st, 0u);
-      __threadfence();
-      atomicAdd(st + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (*verr) { ok = 0; break; }
-        if (clock64() - t0 > 2000000000LL) { atomicExch(st + 2, 1u); ok = 0; break; }
-        __nanosleep(64);
-      }
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(st) : "memory");
+    const long long t0 = clock64();
+    while (true) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(st) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if (*verr) { ok = 0; break; }
+      if (clock64() - t0 > 2000000000LL) { atomicExch(st + 2, 1u); ok = 0; break; }
     }
     __threadfence();
     ok_sh = ok && (*verr == 0);
@@ -388,53 +412,64 @@ __device__ bool grid_sync(unsigned int* st) {
   return ok_sh != 0;
 }
 
-// Reflector of column k from row k (conjugate of the column), by one warp.
-__device__ void house_row(const EigMat& M, int k, int lane) {
+// Reflector of column k from row k by a whole block (block reductions).
+__device__ void house_row_block(const EigMat& M, int k, double* sh, double2* scale_sh) {
   const int m = M.m;
   double2* row = M.H + (size_t)k * m;
   if (k == m - 1) {
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
       M.d[k] = row[k].x;
       M.e[k] = 0.0;
       M.tau[k] = make_double2(0.0, 0.0);
     }
+    __syncthreads();
     return;
   }
   const int n = m - k - 1;
   double2* x = row + k + 1;
   double amax = 0.0;
-  for (int r = lane; r < n; r += 32) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
-  amax = warp_max(amax);
+  for (int r = threadIdx.x; r < n; r += blockDim.x) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
+  amax = -block_min(-amax, sh);
   const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
   double s = 0.0;
-  for (int r = 1 + lane; r < n; r += 32) {
+  for (int r = 1 + threadIdx.x; r < n; r += blockDim.x) {
     const double vx = x[r].x * sinv, vy = x[r].y * sinv;
     s = fma(vx, vx, fma(vy, vy, s));
   }
-  const double xnorm2 = warp_sum(s);
-  const double ar = x[0].x * sinv, ai = -x[0].y * sinv;
-  double beta;
-  double2 tau, sc;
-  if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
-    beta = x[0].x;
-    tau = make_double2(0.0, 0.0);
-    sc = make_double2(0.0, 0.0);
-  } else {
-    const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
-    tau = make_double2((bs - ar) / bs, -ai / bs);
-    const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
-    sc = make_double2(zr / den * sinv, -zi / den * sinv);
-    beta = bs * amax;
-  }
-  const double dk = row[k].x;
-  __syncwarp();
-  if (lane == 0) {
-    M.d[k] = dk;
+  const double xnorm2 = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double ar = x[0].x * sinv, ai = -x[0].y * sinv;
+    double beta;
+    double2 tau, sc;
+    if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
+      beta = x[0].x;
+      tau = make_double2(0.0, 0.0);
+      sc = make_double2(0.0, 0.0);
+    } else {
+      const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
+      tau = make_double2((bs - ar) / bs, -ai / bs);
+      const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
+      sc = make_double2(zr / den * sinv, -zi / den * sinv);
+      beta = bs * amax;
+    }
+    M.d[k] = row[k].x;
     M.e[k] = beta;
     M.tau[k] = tau;
+    *scale_sh = sc;
   }
-  for (int r = lane; r < n; r += 32) x[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(x[r]), sc);
-  __syncwarp();
+  __syncthreads();
+  const double2 sc = *scale_sh;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) x[r] = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(x[r]), sc);
+  __syncthreads();
+}
+
+// alpha = -tau (p^+ v) / 2 from the per-strip partial sums (fixed order)
+__device__ __forceinline__ double2 rank2_alpha(const EigMat& M, int k, int n) {
+  const int ns = (n + TD_STRIP - 1) / TD_STRIP;
+  double2 dot = make_double2(0.0, 0.0);
+  for (int j = 0; j < ns; ++j) dot = cadd(dot, M.part[j]);
+  const double2 t2 = cmul(M.tau[k], dot);
+  return make_double2(-0.5 * t2.x, -0.5 * t2.y);
 }
 
 __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ EigBatch b, int mmax) {
@@ -442,10 +477,17 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ 
   const int gw = blockIdx.x * TD_WARPS + warp, nwarps = gridDim.x * TD_WARPS;
   __shared__ double2 acc_sh[TD_WARPS][TD_STRIP];
   __shared__ double2 pd_sh[TD_STRIP];
-  for (int i = gw; i < b.n; i += nwarps) house_row(b.a[i], 0, lane);
-  if (!grid_sync(b.bar)) return;
+  __shared__ double red_sh[33];
+  __shared__ double2 scale_sh;
+  unsigned int target = 0;  // barrier count expected at the next grid_sync
+  for (int i = blockIdx.x; i < b.n; i += gridDim.x) house_row_block(b.a[i], 0, red_sh, &scale_sh);
+  if (!grid_sync(b.bar, target)) return;
   for (int k = 0; k < mmax - 1; ++k) {
-    // ---- phase V: p = tau A22 v, one strip of columns per block at a time
+    // ---- phase V: p = tau A22 v, one strip of 32 columns per block at a time.  A strip
+    // reads its columns above the diagonal (stored A[r][c] = conj(A[c][r]); the
+    // diagonal is real) and its rows right of the diagonal, so the product is exact
+    // and deterministic without scatter.  Four rows per iteration keep four
+    // independent loads in flight; all sums stay in registers until the end.
     for (int item = blockIdx.x;; item += gridDim.x) {
       int rem = item, mi = -1;
       for (int i = 0; i < b.n; ++i) {
@@ -462,26 +504,39 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ 
       const double2* A = M.H + (size_t)(k + 1) * m + k + 1;
       const int c = c0 + lane;
       double2 acc = make_double2(0.0, 0.0);
-      // p[c] = sum_r A[c][r] v[r]: rows r < c through the stored A[r][c] = conj(A[c][r]),
-      // the diagonal as stored, rows r > c (below) through row c itself
-      for (int r = warp; r < c0 + w; r += TD_WARPS) {
-        if (lane < w && c >= r) {
-          const double2 a = A[(size_t)r * m + c];
-          acc = (c == r) ? cfma(a, v[r], acc) : cfma_conj(a, v[r], acc);
+      const int rmax = c0 + w;
+      for (int r0 = warp; r0 < rmax; r0 += 4 * TD_WARPS) {
+        double2 a[4], vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u * TD_WARPS;
+          const bool ok = r < rmax && lane < w && c >= r;
+          a[u] = ok ? A[(size_t)r * m + c] : make_double2(0.0, 0.0);
+          vv[u] = r < rmax ? v[r] : make_double2(0.0, 0.0);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = cfma_conj(a[u], vv[u], acc);
       }
       acc_sh[warp][lane] = acc;
       __syncthreads();
       const double2 tau = M.tau[k];
       for (int q = warp; q < w; q += TD_WARPS) {
         const int cc = c0 + q;
-        double2 a2 = make_double2(0.0, 0.0);
-        for (int r = cc + 1 + lane; r < n; r += 32) a2 = cfma(A[(size_t)cc * m + r], v[r], a2);
-        a2 = warp_sum2(a2);
+        double2 a2[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                         make_double2(0.0, 0.0)};
+        const double2* rowc = A + (size_t)cc * m;
+        for (int r0 = cc + 1 + lane; r0 < n; r0 += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + 32 * u;
+            if (r < n) a2[u] = cfma(rowc[r], v[r], a2[u]);
+          }
+        }
+        const double2 a2s = warp_sum2(cadd(cadd(a2[0], a2[1]), cadd(a2[2], a2[3])));
         if (lane == 0) {
           double2 p1 = make_double2(0.0, 0.0);
           for (int wq = 0; wq < TD_WARPS; ++wq) p1 = cadd(p1, acc_sh[wq][q]);
-          const double2 pc = cmul(tau, cadd(p1, a2));
+          const double2 pc = cmul(tau, cadd(p1, a2s));
           M.p[cc] = pc;
           pd_sh[q] = cfma_conj(pc, v[cc], make_double2(0.0, 0.0));
         }
@@ -494,9 +549,9 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ 
       }
       __syncthreads();
     }
-    if (!grid_sync(b.bar)) return;
-    // ---- phase R: A22 -= v w^+ + w v^+ on the upper triangle; reflector of column k+1
-    for (int item = gw;; item += nwarps) {
+    if (!grid_sync(b.bar, target)) return;
+    // ---- phase W: w = p + alpha v once per element (alpha from the strip partials)
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x;; item += gridDim.x * blockDim.x) {
       int rem = item, mi = -1;
       for (int i = 0; i < b.n; ++i) {
         const int n = b.a[i].m - k - 1;
@@ -506,31 +561,73 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ 
       }
       if (mi < 0) break;
       const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1, r = rem;
-      const int ns = (n + TD_STRIP - 1) / TD_STRIP;
-      double2 dot = make_double2(0.0, 0.0);
-      for (int j = 0; j < ns; ++j) dot = cadd(dot, M.part[j]);
-      const double2 t2 = cmul(M.tau[k], dot);
-      const double2 alpha = make_double2(-0.5 * t2.x, -0.5 * t2.y);
+      const int m = M.m, n = m - k - 1;
+      const double2 alpha = rank2_alpha(M, k, n);
+      M.pp[rem] = cfma(alpha, M.H[(size_t)k * m + k + 1 + rem], M.p[rem]);
+    }
+    if (!grid_sync(b.bar, target)) return;
+    // ---- phase R: A22 -= v w^+ + w v^+ on the upper triangle.  The first trailing row
+    // of every matrix goes to a whole block, which then builds the reflector of
+    // column k+1 from it (the critical path of the next column); rows >= 1 go to warps.
+    for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
+      const EigMat& M = b.a[mi];
+      const int m = M.m, n = m - k - 1;
+      if (n <= 0) continue;
       const double2* v = M.H + (size_t)k * m + k + 1;
-      const double2* p = M.p;
-      const double2 vr = v[r];
-      const double2 wr = cfma(alpha, vr, p[r]);
-      double2* row = M.H + (size_t)(k + 1 + r) * m + k + 1;
-      for (int cc = r + lane; cc < n; cc += 32) {
+      const double2* wv = M.pp;
+      const double2 vr = v[0];
+      const double2 wr = wv[0];
+      double2* row = M.H + (size_t)(k + 1) * m + k + 1;
+      for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
         const double2 vc = v[cc];
-        const double2 wc = cfma(alpha, vc, p[cc]);
+        const double2 wc = wv[cc];
         double2 a = row[cc];
         a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
         a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
         row[cc] = a;
       }
-      if (r == 0) {
-        __syncwarp();
-        house_row(M, k + 1, lane);
+      __syncthreads();
+      house_row_block(M, k + 1, red_sh, &scale_sh);
+    }
+    for (int item = gw;; item += nwarps) {
+      int rem = item, mi = -1;
+      for (int i = 0; i < b.n; ++i) {
+        const int n = b.a[i].m - k - 1;
+        if (n <= 1) continue;
+        if (rem < n - 1) { mi = i; break; }
+        rem -= n - 1;
+      }
+      if (mi < 0) break;
+      const EigMat& M = b.a[mi];
+      const int m = M.m, n = m - k - 1, r = rem + 1;
+      const double2* v = M.H + (size_t)k * m + k + 1;
+      const double2* p = M.pp;  // w = p + alpha v
+      const double2 vr = v[r];
+      const double2 wr = p[r];
+      double2* row = M.H + (size_t)(k + 1 + r) * m + k + 1;
+      for (int c0 = r + lane; c0 < n; c0 += 128) {
+        double2 a[4], vc[4], pc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = c0 + 32 * u;
+          const bool ok = cc < n;
+          a[u] = ok ? row[cc] : make_double2(0.0, 0.0);
+          vc[u] = ok ? v[cc] : make_double2(0.0, 0.0);
+          pc[u] = ok ? p[cc] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int cc = c0 + 32 * u;
+          if (cc < n) {
+            const double2 wc = pc[u];
+            a[u].x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc[u].x + wr.y * vc[u].y;
+            a[u].y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc[u].x - wr.x * vc[u].y;
+            row[cc] = a[u];
+          }
+        }
       }
     }
-    if (!grid_sync(b.bar)) return;
+    if (!grid_sync(b.bar, target)) return;
   }
 }
 
@@ -562,6 +659,7 @@ int eig_tridiagonalize(const EigBatch& b, cudaStream_t s) {
     grid = std::max(1, sms * std::min(per_sm, 2));
   }
   int mmax = mm;
+  cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
   void* args[] = {const_cast<EigBatch*>(&b), &mmax};
   if (cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(grid), dim3(TD_THREADS), args, 0, s) != cudaSuccess)
     return -1;
@@ -573,7 +671,7 @@ int eig_bisect(const EigBatch& b, cudaStream_t s) {
   int km = 0;
   for (int i = 0; i < b.n; ++i) km = std::max(km, std::min(b.a[i].kmax, b.a[i].m));
   if (km == 0) return 0;
-  k_bisect<<<dim3((km + 31) / 32, b.n), 32, 0, s>>>(b);  // one warp per block spreads the chains over SMs
+  k_bisect<<<dim3((km + 3) / 4, b.n), 128, 0, s>>>(b);  // four eigenvalues (warps) per block
   return 1;
 }
 

@@ -95,6 +95,7 @@ struct EigMat {
   double2* tau;      // Householder scalars [m]
   double2* part;     // partial dot products [EIG_PARTS], one per 32-column strip
   double2* p;        // p = tau A22 v [m]
+  double2* pp;       // w = p + alpha v of the current column [m]
   double* evals;     // eigenvalues, descending [kmax]
   double* trace;     // [1] trace of H (sum of Re H_rr), taken before reduction
   double* Z;         // m x K real eigenvectors of T (row-major, ld = K)
