@@ -82,10 +82,11 @@ int tebd_step(tebd_handle h, int n_steps);
 
 /* Device bytes a handle with these sizes holds once stepped and measured
  * (state, gates, workspace for min(triples per layer, 24, max_slots > 0 ?
- * max_slots : 24) concurrent local updates, measurement buffers), written to
- * *bytes.  Host-only arithmetic: used to admit simulations by an HBM budget
- * before creating them. */
-int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, double* bytes);
+ * max_slots : 24) concurrent local updates, measurement buffers; precision 1
+ * adds the digit planes of the mixed path's Gram and projection products),
+ * written to *bytes.  Host-only arithmetic: used to admit simulations by an
+ * HBM budget before creating them.  precision must be 0 or 1. */
+int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
 /* Batched form: advance n distinct handles (simulations with any L, n_max,
  * chi_max and parameters) by n_steps full steps together.  Within every
@@ -177,9 +178,14 @@ int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K,
  * row-major with leading dimensions in complex elements), A: M x K, op(B): K x N
  * with opB = 0 (B stored K x N) or 1 (B^+, B stored N x K), C: M x N.
  * precision 0: FP64 on the CUDA cores; 1: split 3xTF32 on the tcgen05 tensor
- * cores with FP32 accumulation (relative error ~5e-7 of |A||B|).  Enqueued on
- * cuda_stream (NULL = legacy default stream), not synchronised.  Sizes >= 1,
- * leading dimensions >= the row lengths; otherwise TEBD_ERR_ARG. */
+ * cores with FP32 accumulation (relative error ~5e-7 of |A||B|); 2: FP64-accurate
+ * exact-digit products on the bf16 tensor cores (the mixed path's Gram and
+ * projection engine: eight 7-bit digits per row-scaled real, exact integer
+ * accumulation, one final rounding; error below 2^-53 max|A_i.| max|B_.j| K).
+ * Precision 2 allocates and frees its digit workspace stream-ordered on
+ * cuda_stream.  Enqueued on cuda_stream (NULL = legacy default stream), not
+ * synchronised.  Sizes >= 1, leading dimensions >= the row lengths; otherwise
+ * TEBD_ERR_ARG. */
 int tebd_zgemm(int precision, int opB, int M, int N, int K, double alpha, const double* A, long long lda,
                const double* B, long long ldb, double* C, long long ldc, void* cuda_stream);
 

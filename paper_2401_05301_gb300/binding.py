@@ -30,7 +30,7 @@ SIGNATURES = {
     "tebd_step": (_c_int, [_c_void_p, _c_int]),
     "tebd_layer": (_c_int, [_c_void_p, _c_int, _c_int]),
     "tebd_batch_step": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, _c_int]),
-    "tebd_estimate_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _P_double]),
+    "tebd_estimate_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _P_double]),
     "tebd_measure": (_c_int, [_c_void_p, _P_double, _P_double]),
     "tebd_stats": (_c_int, [_c_void_p, _P_double, _P_double, _P_int]),
     "tebd_bond_dims": (_c_int, [_c_void_p, _P_int]),
@@ -82,10 +82,10 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(_P_double)
 
 
-def estimate_bytes(L, n_max, chi_max, max_slots=0) -> float:
+def estimate_bytes(L, n_max, chi_max, max_slots=0, precision=0) -> float:
     """Device bytes a simulation of these sizes will hold (tebd_estimate_bytes)."""
     out = _c_double()
-    _check(load().tebd_estimate_bytes(L, n_max, chi_max, max_slots, ctypes.byref(out)), "tebd_estimate_bytes")
+    _check(load().tebd_estimate_bytes(L, n_max, chi_max, max_slots, precision, ctypes.byref(out)), "tebd_estimate_bytes")
     return out.value
 
 

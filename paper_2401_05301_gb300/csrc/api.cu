@@ -27,6 +27,7 @@ struct Slot {
   double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *pp, *U;
   double *d, *e, *evals, *Z, *Z2, *S, *work, *s_sorted, *scal;  // scal: [0] trace [1] norm [2] w
   int *perm, *chi;
+  void* oz;  // digit planes of the mixed path's Gram and projection products (null in FP64)
 };
 
 struct Triple {
@@ -199,12 +200,22 @@ int max_triples_per_layer(int L) {
 
 // Device bytes of one workspace slot (one triple in flight) for bond capacity
 // capmax, local dimension d and bond cap chi_max.
-double slot_bytes_for(long long capmax, long long d, long long chi_max) {
+// Digit workspace of the mixed path: the largest of the Gram H1 (m x m over n1),
+// projection Y1 (K x n1 over m) and projection Y2 (K x m over m) products.
+double oz_slot_bytes(long long capmax, long long d, long long chi_max) {
+  const long long mm = capmax * d, n1max = d * d * capmax, kc = std::min<long long>(mm, chi_max);
+  return (double)std::max({oz_workspace_bytes((int)mm, (int)mm, (int)n1max, true),
+                           oz_workspace_bytes((int)kc, (int)n1max, (int)mm, false),
+                           oz_workspace_bytes((int)kc, (int)mm, (int)mm, false)});
+}
+
+double slot_bytes_for(long long capmax, long long d, long long chi_max, int precision) {
   const long long D = d * d * d, mm = capmax * d, n1max = d * d * capmax;
   const long long kc = std::min<long long>(mm, chi_max);
   return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 4.0 * mm +
                  EIG_PARTS + kc * mm) +
-         8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1);
+         8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1) +
+         (precision == 1 ? oz_slot_bytes(capmax, d, chi_max) : 0.0);
 }
 
 std::vector<int> bond_caps(int L, int d, int chi_max) {
@@ -224,7 +235,7 @@ int alloc_workspace(tebd_ctx* c) {
   c->kcap = std::min<long long>(c->mmax, c->chi_max);
   if (c->mmax > 12288) return TEBD_ERR_ARG;  // the reduction's partial sums are sized for m <= 12288
   const long long D = c->D, mm = c->mmax, kc = c->kcap;
-  const double slot_bytes = slot_bytes_for(capmax, d, c->chi_max);
+  const double slot_bytes = slot_bytes_for(capmax, d, c->chi_max, c->precision);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
@@ -254,7 +265,8 @@ int alloc_workspace(tebd_ctx* c) {
     S.scal = dalloc<double>(c, 4);
     S.perm = dalloc<int>(c, mm);
     S.chi = dalloc<int>(c, 1);
-    if (!S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.pp || !S.U || !S.d || !S.e ||
+    if (c->precision == 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max));
+    if ((c->precision == 1 && !S.oz) || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.pp || !S.U || !S.d || !S.e ||
         !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
       if (s == 0) return TEBD_ERR_OOM;
       break;
@@ -262,6 +274,14 @@ int alloc_workspace(tebd_ctx* c) {
     c->slots.push_back(S);
   }
   return ensure_pinned(c, (size_t)c->slots.size() * (c->kcap + 8) + 64);
+}
+
+// The mixed path's digit planes, for workspaces allocated while the handle was FP64.
+int ensure_oz(tebd_ctx* c) {
+  for (Slot& S : c->slots)
+    if (!S.oz && !(S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(c->capmax, c->d, c->chi_max))))
+      return TEBD_ERR_OOM;
+  return TEBD_OK;
 }
 
 // PTEBD_DEBUG=1: synchronise after each stage and print a summary of a buffer
@@ -450,12 +470,49 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   return TEBD_OK;
 }
 
+// Mixed path, exact-digit tensor-core products (FP64 accuracy):
+// Gram H = (lam X)(lam X)^+ of X (m x n, row-major), rows scaled by lam[r / d].
+OzProb oz_gram(const double2* X, int m, int n, const double* lam, int d, double2* H, void* ws) {
+  OzProb q{};
+  q.a = OzOperand{X, n, 1, nullptr, 1, 0};
+  q.M = q.N = m;
+  q.K = n;
+  q.C = H;
+  q.ldc = m;
+  q.alpha = 1.0;
+  q.s_row = q.s_col = lam;
+  q.row_div = q.col_div = d;
+  q.herm = q.gram = 1;
+  q.ws = ws;
+  return q;
+}
+
+// Projection Y = U^+ (lam X): U holds K eigenvectors as rows of length m, X is m x n.
+OzProb oz_project(const double2* U, int K, int m, const double* lam, int d, const double2* X, int n, double2* Y,
+                  void* ws) {
+  OzProb q{};
+  q.a = OzOperand{U, m, 1, lam, d, 1};
+  q.b = OzOperand{X, 1, n, nullptr, 1, 0};
+  q.M = K;
+  q.N = n;
+  q.K = m;
+  q.C = Y;
+  q.ldc = n;
+  q.alpha = 1.0;
+  q.row_div = q.col_div = 1;
+  q.ws = ws;
+  return q;
+}
+
 // One batch of independent local updates (disjoint triples, possibly of
 // different simulations), driven on c's stream.  c->precision selects the
 // contraction path for the whole batch.
 int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   cudaStream_t s = c->stream;
   const bool mixed = c->precision == 1;
+  if (mixed)
+    for (auto& T : ts)
+      if (int r = ensure_oz(T.h)) return r;
   for (auto& T : ts) {
     const tebd_ctx* o = T.h;
     T.chl = o->chi[T.i]; T.c1 = o->chi[T.i + 1]; T.c2 = o->chi[T.i + 2]; T.chr = o->chi[T.i + 3];
@@ -465,6 +522,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   // theta~ = B_i B_{i+1} B_{i+2}; C = G theta~; Gram H1 = (lam C)(lam C)^+
   {
     Gemm g1(true, OP_N, OP_N), g2(true, OP_N, OP_N), g3(true, OP_N, OP_N), g4(true, OP_N, OP_C);
+    std::vector<OzProb> oz4;
     for (auto& T : ts) {
       tebd_ctx* o = T.h;
       const int d = o->d, D = o->D;
@@ -479,6 +537,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       p4.s_row = p4.s_col = o->lam[T.i];
       p4.row_div = p4.col_div = d;
       p4.herm = 1;
+      oz4.push_back(oz_gram(S.Cb, T.m1, T.n1, o->lam[T.i], d, S.H, S.oz));
     }
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
@@ -495,7 +554,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
-      c->launches += g4.launch(s);
+      c->launches += mixed ? oz_gemm_launch(oz4, c->d_status, s) : g4.launch(s);
     }
     if (int r = check_launch(c)) return r;
     for (auto& T : ts) {
@@ -510,16 +569,18 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   if (int r = eigen_stage(c, ts, false)) return r;
   {  // Y1 = U1^+ (lam C)
     Gemm g5(true, OP_CJ, OP_N);
+    std::vector<OzProb> oz5;
     for (auto& T : ts) {
       const Slot& S = T.h->slots[T.slot];
       GemmProb& p = g5.add(T.K1, T.n1, T.m1, S.U, T.m1, S.Cb, T.n1, S.Th, T.n1);
       p.s_red = T.h->lam[T.i];
       p.red_div = T.h->d;
+      oz5.push_back(oz_project(S.U, T.K1, T.m1, T.h->lam[T.i], T.h->d, S.Cb, T.n1, S.Th, S.oz));
     }
     double w = 0.0;
     for (auto& T : ts) w += 8.0 * (double)T.K1 * T.n1 * T.m1;
     ProfScope ps(c, TEBD_PROF_PROJECT, w);
-    c->launches += g5.launch(s);
+    c->launches += mixed ? oz_gemm_launch(oz5, c->d_status, s) : g5.launch(s);
   }
   for (auto& T : ts) debug_dump(c, "Y1", T.i, T.h->slots[T.slot].Th, 2ull * T.K1 * T.n1);
   if (int r = truncate_stage(c, ts, false)) return r;
@@ -535,6 +596,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     // B_i = C V1 / ||s||;  Gram H2 = (lam' V1^+)(lam' V1^+)^+ viewed as (chi' d) x (d chr)
     Gemm g6(true, OP_N, OP_C), g7(true, OP_N, OP_C);
+    std::vector<OzProb> oz7;
     for (auto& T : ts) {
       tebd_ctx* o = T.h;
       const int d = o->d;
@@ -547,6 +609,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       p7.s_row = p7.s_col = o->lam[T.i + 1];
       p7.row_div = p7.col_div = d;
       p7.herm = 1;
+      oz7.push_back(oz_gram(S.V1h, T.m2, T.n2, o->lam[T.i + 1], d, S.H, S.oz));
     }
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
@@ -559,23 +622,25 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
-      c->launches += g7.launch(s);
+      c->launches += mixed ? oz_gemm_launch(oz7, c->d_status, s) : g7.launch(s);
     }
     if (int r = check_launch(c)) return r;
   }
   if (int r = eigen_stage(c, ts, true)) return r;
   {  // Y2 = U2^+ (lam' V1^+)
     Gemm g8(true, OP_CJ, OP_N);
+    std::vector<OzProb> oz8;
     for (auto& T : ts) {
       const Slot& S = T.h->slots[T.slot];
       GemmProb& p = g8.add(T.K2, T.n2, T.m2, S.U, T.m2, S.V1h, T.n2, S.Th, T.n2);
       p.s_red = T.h->lam[T.i + 1];
       p.red_div = T.h->d;
+      oz8.push_back(oz_project(S.U, T.K2, T.m2, T.h->lam[T.i + 1], T.h->d, S.V1h, T.n2, S.Th, S.oz));
     }
     double w = 0.0;
     for (auto& T : ts) w += 8.0 * (double)T.K2 * T.n2 * T.m2;
     ProfScope ps(c, TEBD_PROF_PROJECT, w);
-    c->launches += g8.launch(s);
+    c->launches += mixed ? oz_gemm_launch(oz8, c->d_status, s) : g8.launch(s);
   }
   if (int r = truncate_stage(c, ts, true)) return r;
   {
@@ -690,9 +755,35 @@ const char* tebd_strerror(int status) {
 
 int tebd_zgemm(int precision, int opB, int M, int N, int K, double alpha, const double* A, long long lda,
                const double* B, long long ldb, double* C, long long ldc, void* cuda_stream) {
-  if ((precision != 0 && precision != 1) || (opB != 0 && opB != 1)) return TEBD_ERR_ARG;
+  if (precision < 0 || precision > 2 || (opB != 0 && opB != 1)) return TEBD_ERR_ARG;
   if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !is_fin(alpha)) return TEBD_ERR_ARG;
   if (lda < K || ldc < N || ldb < (opB ? K : N)) return TEBD_ERR_ARG;
+  if (precision == 2) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    OzProb q{};
+    q.a = OzOperand{reinterpret_cast<const double2*>(A), lda, 1, nullptr, 1, 0};
+    q.b = opB ? OzOperand{reinterpret_cast<const double2*>(B), ldb, 1, nullptr, 1, 1}
+              : OzOperand{reinterpret_cast<const double2*>(B), 1, ldb, nullptr, 1, 0};
+    q.M = M;
+    q.N = N;
+    q.K = K;
+    q.C = reinterpret_cast<double2*>(C);
+    q.ldc = ldc;
+    q.alpha = alpha;
+    q.row_div = q.col_div = 1;
+    if (cudaMallocAsync(&q.ws, oz_workspace_bytes(M, N, K, false), st) != cudaSuccess) {
+      cudaGetLastError();
+      return TEBD_ERR_OOM;
+    }
+    try {
+      oz_gemm_launch({q}, nullptr, st);
+    } catch (...) {
+      cudaFreeAsync(q.ws, st);
+      return TEBD_ERR_OOM;
+    }
+    cudaFreeAsync(q.ws, st);
+    return cudaGetLastError() == cudaSuccess ? TEBD_OK : TEBD_ERR_CUDA;
+  }
   try {
     Gemm g(true, OP_N, opB ? OP_C : OP_N);
     GemmProb& p = g.add(M, N, K, A, lda, B, ldb, C, ldc);
@@ -887,8 +978,9 @@ int tebd_step(tebd_handle h, int n_steps) {
   return TEBD_OK;
 }
 
-int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, double* bytes) {
+int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes) {
   if (!bytes || L < 3 || n_max < 1 || n_max > 7 || chi_max < 1 || max_slots < 0) return TEBD_ERR_ARG;
+  if (precision != 0 && precision != 1) return TEBD_ERR_ARG;
   const int d = n_max + 1, D = d * d * d;
   const std::vector<int> cap = bond_caps(L, d, chi_max);
   double b = 0.0;
@@ -901,7 +993,7 @@ int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, double* by
   b += 16.0 * 2.0 * (L - 2) * (double)D * D;  // gates
   int slots = std::min(max_triples_per_layer(L), MAX_SLOTS);
   if (max_slots > 0) slots = std::min(slots, max_slots);
-  b += slots * slot_bytes_for(capmax, d, chi_max);
+  b += slots * slot_bytes_for(capmax, d, chi_max, precision);
   b += 16.0 * MEAS_CHUNK * (2.0 * capmax * d * capmax + 2.0 * capmax * capmax) + 24.0 * L;  // measurement
   *bytes = b;
   return TEBD_OK;

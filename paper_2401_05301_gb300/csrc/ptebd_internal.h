@@ -65,6 +65,66 @@ struct TcGemmBatch {
 };
 int tc_gemm_launch(const std::vector<TcGemmProb>& probs, int* status, cudaStream_t s);
 
+// ---- FP64-accurate complex GEMM on bf16 tensor cores, exact digit splitting (kernels_ozaki.cu)
+// C[i][j] = alpha * s_row[i / row_div] * s_col[j / col_div] * sum_k a(i, k) b(j, k)
+// with a(i, k) = op(X_a[i * rs + k * ks]) * scale[k / scale_div] (op: conj if set), b likewise.
+struct OzOperand {
+  const double2* X;
+  long long rs, ks;
+  const double* scale;  // optional factor along the reduction index
+  int scale_div, conj;
+};
+struct OzProb {
+  OzOperand a, b;  // b is ignored when gram is set
+  int M, N, K;
+  double2* C;
+  long long ldc;
+  double alpha;
+  const double* s_row;
+  const double* s_col;
+  int row_div, col_div;
+  int herm;  // Hermitian result: only j <= i is computed, then mirrored (needs gram)
+  int gram;  // b(j, k) = conj(a(j, k)), N = M: the digits of a serve both operands
+  void* ws;  // oz_workspace_bytes(M, N, K, gram) bytes, 256-byte aligned, owned by the caller
+};
+constexpr int OZ_MAXP = 16;
+struct OzPackJob {
+  const double2* X;
+  long long rs, ks;
+  const double* scale;
+  int scale_div, conj, rows, K, nrb, nkt;
+  uint16_t* P0;  // digit plane written with form type0 (null: none)
+  uint16_t* P1;
+  int type0, type1;
+  int* e;  // row exponents [nrb * 32]
+};
+struct OzPackBatch {
+  OzPackJob job[2 * OZ_MAXP];
+  int block_start[2 * OZ_MAXP + 1];
+  int njob;
+};
+struct OzTile {
+  const uint16_t* DA;
+  const uint16_t* D1;
+  const uint16_t* D2;
+  const int* eA;
+  const int* eB;
+  double2* C;
+  long long ldc;
+  double alpha;
+  const double* s_row;
+  const double* s_col;
+  int row_div, col_div, M, N, nkt, nrbA, nrbB, herm, tiles_n;
+};
+struct OzGemmBatch {
+  OzTile p[OZ_MAXP];
+  int tile_start[OZ_MAXP + 1];
+  int nprob;
+  int* status;  // set to TEBD_ERR_TIMEOUT if a bounded wait runs out
+};
+size_t oz_workspace_bytes(int M, int N, int K, bool gram);
+int oz_gemm_launch(const std::vector<OzProb>& probs, int* status, cudaStream_t s);
+
 class Gemm {
  public:
   Gemm(bool complex_, int opA, int opB) : cplx_(complex_), opA_(opA), opB_(opB) {}

@@ -92,7 +92,7 @@ class Server:
         self.peak_active = 0
 
     def footprint(self, req: Request) -> float:
-        return self.estimate_fn(req.L, req.n_max, req.chi_max, req.max_slots)
+        return self.estimate_fn(req.L, req.n_max, req.chi_max, req.max_slots, self.precision)
 
     def _admit(self, req: Request, now: float) -> _Active:
         sim = self.sim_factory(req.L, req.n_max, req.chi_max, req.U, req.J, req.Jnnn, req.K, req.jc, req.dt,

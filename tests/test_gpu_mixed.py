@@ -68,6 +68,37 @@ def test_zgemm_tf32x3_no_accumulation_bias(lib, K):
     assert abs(np.mean(err.real)) < 1e-7
 
 
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (37, 5, 3), (128, 32, 16), (300, 200, 70), (129, 257, 300),
+                                   (64, 600, 125), (256, 96, 1030)])
+@pytest.mark.parametrize("opB", [0, 1])
+def test_zgemm_exact_digits_matches_fp64(lib, M, N, K, opB):
+    """precision 2 (exact-digit products on the bf16 tensor cores) against numpy
+    FP64: rows spanning 30 orders of magnitude, error below 2e-15 of |A||B|
+    (the FP64 path's own bound here is 1e-14)."""
+    rng = np.random.default_rng(7 * M + 3 * N + K + opB)
+    A = (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * 10.0 ** rng.uniform(-15, 15, (M, 1))
+    Bs = (K, N) if opB == 0 else (N, K)
+    B = (rng.standard_normal(Bs) + 1j * rng.standard_normal(Bs)) * 10.0 ** rng.uniform(-8, 8, (Bs[0], 1))
+    opb = B if opB == 0 else B.conj().T
+    ref = 1.3 * (A @ opb)
+    scale = 1.3 * (np.abs(A) @ np.abs(opb))
+    c2 = _zgemm(lib, 2, opB, A, B, 1.3)
+    err = np.max(np.abs(c2 - ref) / scale)
+    print(f"exact-digit zgemm {M}x{N}x{K} opB={opB}: max error / (|A||B|) = {err:.2e}")
+    assert err < 2e-15, err
+
+
+def test_zgemm_exact_digits_gram_is_hermitian(lib):
+    """A A^+ through precision 2: Hermitian to the last bit on the diagonal's
+    imaginary part (digits of -x are the negated digits of x)."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((200, 333)) + 1j * rng.standard_normal((200, 333))
+    H = _zgemm(lib, 2, 1, A, A)
+    assert np.all(np.diag(H).imag == 0.0)
+    ref = A @ A.conj().T
+    assert np.max(np.abs(H - ref)) / np.max(np.abs(ref)) < 1e-15
+
+
 def _compare_mixed(lib, wl, n_steps, every):
     from paper_2401_05301_gb300 import TEBD
     args = dict(L=wl.L, n_max=wl.n_max, chi_max=wl.chi_max, U=wl.U, J=wl.J, Jnnn=wl.Jnnn, K=wl.K, jc=wl.jc,

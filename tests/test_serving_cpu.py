@@ -40,7 +40,7 @@ def _server(budget, clock, log):
             s.steps += n
         clock.t += 0.1
     return serving.Server(budget, sim_factory=FakeSim, step_fn=step, clock=clock,
-                          estimate_fn=lambda L, n_max, chi, slots: 1.0 * L)
+                          estimate_fn=lambda L, n_max, chi, slots, precision: 1.0 * L)
 
 
 def _req(i, t, L, steps):
