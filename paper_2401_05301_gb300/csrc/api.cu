@@ -24,9 +24,10 @@ constexpr int MAX_SLOTS = 24;
 constexpr int MEAS_CHUNK = GEMM_MAXP;
 
 struct Slot {
-  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *pp, *U;
+  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *U;
   double *d, *e, *evals, *Z, *Z2, *S, *work, *s_sorted, *scal;  // scal: [0] trace [1] norm [2] w
   int *perm, *chi;
+  double2* pan;  // panel arrays of the blocked tridiagonal reduction
   void* oz;  // digit planes of the mixed path's Gram and projection products (null in FP64)
 };
 
@@ -212,9 +213,9 @@ double oz_slot_bytes(long long capmax, long long d, long long chi_max) {
 double slot_bytes_for(long long capmax, long long d, long long chi_max, int precision) {
   const long long D = d * d * d, mm = capmax * d, n1max = d * d * capmax;
   const long long kc = std::min<long long>(mm, chi_max);
-  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 4.0 * mm +
+  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 3.0 * mm +
                  EIG_PARTS + kc * mm) +
-         8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1) +
+         8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1) + 16.0 * eig_panel_doubles2((int)mm) +
          (precision == 1 ? oz_slot_bytes(capmax, d, chi_max) : 0.0);
 }
 
@@ -252,7 +253,6 @@ int alloc_workspace(tebd_ctx* c) {
     S.tau = dalloc<double2>(c, mm);
     S.part = dalloc<double2>(c, EIG_PARTS);
     S.p = dalloc<double2>(c, mm);
-    S.pp = dalloc<double2>(c, mm);
     S.U = dalloc<double2>(c, kc * mm);
     S.d = dalloc<double>(c, mm);
     S.e = dalloc<double>(c, mm);
@@ -265,8 +265,9 @@ int alloc_workspace(tebd_ctx* c) {
     S.scal = dalloc<double>(c, 4);
     S.perm = dalloc<int>(c, mm);
     S.chi = dalloc<int>(c, 1);
+    S.pan = dalloc<double2>(c, eig_panel_doubles2((int)mm));
     if (c->precision == 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max));
-    if ((c->precision == 1 && !S.oz) || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.pp || !S.U || !S.d || !S.e ||
+    if ((c->precision == 1 && !S.oz) || !S.pan || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
         !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
       if (s == 0) return TEBD_ERR_OOM;
       break;
@@ -321,13 +322,16 @@ const double2* gate_ptr(const tebd_ctx* c, int i, int tidx) {
 // slot and options belong to its owner T.h (several simulations may share a batch).
 int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   EigBatch eb{};
+  void* oz_ws[EIG_MAXP] = {};
   eb.n = (int)ts.size();
   eb.bar = c->d_bar;
   for (size_t t = 0; t < ts.size(); ++t) {
     const Slot& S = ts[t].h->slots[ts[t].slot];
     EigMat& M = eb.a[t];
-    M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p; M.pp = S.pp;
+    M.H = S.H; M.d = S.d; M.e = S.e; M.tau = S.tau; M.part = S.part; M.p = S.p;
     M.evals = S.evals; M.trace = S.scal; M.Z = S.Z; M.Z2 = S.Z2; M.S = S.S; M.work = S.work; M.U = S.U;
+    M.pan = S.pan;
+    oz_ws[t] = S.oz;
     M.m = second ? ts[t].m2 : ts[t].m1;
     const int n = second ? ts[t].n2 : ts[t].n1;
     // at most min(m, n) singular values are non-zero: noise eigenvalues of a
@@ -340,7 +344,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     for (int t = 0; t < eb.n; ++t) w += 16.0 / 3.0 * std::pow((double)eb.a[t].m, 3);
     ProfScope ps(c, TEBD_PROF_TRIDIAG, w);
     c->launches += eig_trace(eb, c->stream);
-    const int nl = eig_tridiagonalize(eb, c->stream);
+    const int nl = eig_tridiagonalize(eb, c->precision == 1, oz_ws, c->d_status, c->stream);
     if (nl < 0) {
       cudaGetLastError();
       std::fprintf(stderr, "ptebd: cooperative launch of the tridiagonal reduction refused\n");

@@ -364,22 +364,21 @@ __global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ Ei
   }
 }
 
-// ---- persistent Householder reduction ----------------------------------------------------
-// One cooperative launch reduces every matrix of the batch.  Only the upper
-// triangle A[r][c], c >= r, of the trailing matrix is kept current (half the
-// rank-2 work of full storage); row k beyond the diagonal holds v_k.  Per
-// column k: phase V computes p = tau A22 v by strips of 32 columns (each strip
-// reads its columns above the diagonal and its rows right of it, so the
-// product is exact and deterministic without scatter), phase W forms
-// w = p + alpha v once per element, and phase R applies the rank-2 update row
-// by row; the block that owns the first trailing row then builds the reflector
-// of column k+1 from it.  Every FP64 operation is scarce on this part, so sums
-// stay in registers and no per-element quantity is recomputed.  Three grid
-// barriers per column.
+// ---- blocked Householder reduction ---------------------------------------------------------
+// Panels of TD_NB columns.  Within a panel the trailing matrix is left as it was
+// at the panel start; each column's Hermitian product runs on that stored upper
+// triangle (read once per column, as balanced slabs) and is corrected with the
+// panel's earlier (v_i, w_i).  Only the next pivot row is brought up to date, by
+// all blocks.  After the panel the trailing matrix takes the whole rank-2*TD_NB
+// update as one Hermitian matrix product (tensor cores in the mixed path).  Every
+// FP64 operation is scarce on this part, so sums stay in registers and every
+// reduction has a fixed order (bitwise reproducible).  Three grid barriers per column.
 
 constexpr int TD_THREADS = 256;
 constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
+constexpr int TD_NB = 32;      // columns per panel of the blocked reduction
+constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian product
 
 
 // Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
@@ -472,22 +471,160 @@ __device__ __forceinline__ double2 rank2_alpha(const EigMat& M, int k, int n) {
   return make_double2(-0.5 * t2.x, -0.5 * t2.y);
 }
 
-__global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ EigBatch b, int mmax) {
+// Panel arrays of a matrix: VW[r] = (v_0..v_{NB-1}, w_0..w_{NB-1})(r), WV[r] the
+// same with the halves swapped (the second operand of the trailing update), the
+// per-strip partial dots of the panel corrections, and the partial sums of the
+// Hermitian product (64 per slab: column part, then row part).
+__device__ __forceinline__ double2* pan_vw(const EigMat& M) { return M.pan; }
+__device__ __forceinline__ double2* pan_wv(const EigMat& M) { return M.pan + (size_t)M.m * 2 * TD_NB; }
+__device__ __forceinline__ double2* pan_xy(const EigMat& M) { return M.pan + (size_t)M.m * 4 * TD_NB; }
+__device__ __forceinline__ double2* pan_hp(const EigMat& M) {
+  return M.pan + (size_t)M.m * 4 * TD_NB + (size_t)EIG_PARTS * 2 * TD_NB;
+}
+
+// w = p + alpha v of column kp (panel index jp), stored as column jp of W.
+__device__ void finish_w(const EigMat& M, int kp, int jp, double2 alpha) {
+  const int m = M.m, n = m - kp - 1;
+  if (n <= 0) return;
+  const double2* v = M.H + (size_t)kp * m + kp + 1;
+  double2* VW = pan_vw(M);
+  double2* WV = pan_wv(M);
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double2 w = cfma(alpha, v[r], M.p[r]);
+    const size_t row = (size_t)(kp + 1 + r) * 2 * TD_NB;
+    VW[row + TD_NB + jp] = w;
+    WV[row + jp] = w;
+  }
+}
+
+// Blocked Householder tridiagonalisation, one panel of columns [k0, k1) per
+// cooperative launch (the trailing matrix from k0 on is current when it starts).
+// Column k (panel index j) is reduced against A(k) = A(k0) - sum_{i<j} (v_i w_i^+ +
+// w_i v_i^+) without forming A(k):
+//   phase 1 (a block per matrix): w of column k-1 and the last term of row k (see
+//           phase 3); the reflector of column k (v_k, tau_k).
+//   phase 2 (slabs of 32 x TD_CHUNK): h = A(k0) v over the stored upper triangle,
+//           and per-strip partials of w_i^+ v and v_i^+ v.
+//   phase 3 (strips of 32): p = tau (h - sum_i (v_i (w_i^+ v) + w_i (v_i^+ v))), the
+//           strip partials of p^+ v for alpha, and row k+1 brought to A(k+1) except
+//           for the part of column k's own term that needs alpha.
+// After the panel, the caller applies A -= V W^+ + W V^+ to rows and columns >= k1
+// as one Hermitian rank-2*NB matrix product.
+__global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_constant__ EigBatch b, int k0, int k1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * TD_WARPS + warp, nwarps = gridDim.x * TD_WARPS;
   __shared__ double2 acc_sh[TD_WARPS][TD_STRIP];
-  __shared__ double2 pd_sh[TD_STRIP];
+  __shared__ double2 xy_sh[2 * TD_NB];
+  __shared__ double2 vk_sh[2 * TD_NB];
+  __shared__ double2 pv_sh[TD_WARPS][TD_STRIP];
+  __shared__ double2 rv_sh[TD_WARPS][TD_STRIP];
   __shared__ double red_sh[33];
   __shared__ double2 scale_sh;
   unsigned int target = 0;  // barrier count expected at the next grid_sync
-  for (int i = blockIdx.x; i < b.n; i += gridDim.x) house_row_block(b.a[i], 0, red_sh, &scale_sh);
-  if (!grid_sync(b.bar, target)) return;
-  for (int k = 0; k < mmax - 1; ++k) {
-    // ---- phase V: p = tau A22 v, one strip of 32 columns per block at a time.  A strip
-    // reads its columns above the diagonal (stored A[r][c] = conj(A[c][r]); the
-    // diagonal is real) and its rows right of the diagonal, so the product is exact
-    // and deterministic without scatter.  Four rows per iteration keep four
-    // independent loads in flight; all sums stay in registers until the end.
+  for (int k = k0; k < k1; ++k) {
+    const int j = k - k0;
+    // ---- phase 1
+    for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
+      const EigMat& M = b.a[mi];
+      const int m = M.m;
+      if (k >= m) continue;
+      double2* row = M.H + (size_t)k * m;
+      if (j > 0) {
+        // Row k was brought to A(k) in phase 3 of column k-1 except for the alpha
+        // part of that column's own term: with v_{k-1}(k) = 1 and w = p + alpha v it
+        // is (p(k) + 2 Re alpha) conj(v_{k-1}(c)).
+        const double2 alpha = rank2_alpha(M, k - 1, m - k);
+        finish_w(M, k - 1, j - 1, alpha);
+        const double2 sft = make_double2(M.p[0].x + 2.0 * alpha.x, M.p[0].y);
+        const double2* vp = M.H + (size_t)(k - 1) * m;
+        for (int c = k + threadIdx.x; c < m; c += blockDim.x) row[c] = csub(row[c], cmul(sft, cconj(vp[c])));
+      }
+      __syncthreads();
+      house_row_block(M, k, red_sh, &scale_sh);
+      double2* VWm = pan_vw(M);
+      double2* WVm = pan_wv(M);
+      for (int r = k + 1 + threadIdx.x; r < m; r += blockDim.x) {
+        const double2 v = row[r];
+        VWm[(size_t)r * 2 * TD_NB + j] = v;
+        WVm[(size_t)r * 2 * TD_NB + TD_NB + j] = v;
+      }
+    }
+    if (!grid_sync(b.bar, target)) return;
+    // ---- phase 2: h = A(k0) v by slabs.  Item (s, q) covers strip s (32 columns) and
+    // chunk q (TD_CHUNK indices) of the trailing set: the column part reads the stored
+    // rows r in chunk q above the strip's columns (r <= c, used as conj(A[r][c]) v[r]),
+    // the row part reads the strip's rows at columns c > row in chunk q.  Every item
+    // holds about 32 x TD_CHUNK elements, so the work balances across blocks.
+    for (int item = blockIdx.x;; item += gridDim.x) {
+      int rem = item, mi = -1;
+      for (int i = 0; i < b.n; ++i) {
+        const int n = b.a[i].m - k - 1;
+        const int ni = (n > 0) ? ((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK) : 0;
+        if (rem < ni) { mi = i; break; }
+        rem -= ni;
+      }
+      if (mi < 0) break;
+      const EigMat& M = b.a[mi];
+      const int m = M.m, n = m - k - 1;
+      const int nq = (n + TD_CHUNK - 1) / TD_CHUNK;
+      const int sidx = rem / nq, q = rem % nq;
+      const int c0 = sidx * TD_STRIP, w = min(TD_STRIP, n - c0);
+      const int q0 = q * TD_CHUNK, q1 = min(n, q0 + TD_CHUNK);
+      const double2* v = M.H + (size_t)k * m + k + 1;
+      const double2* A = M.H + (size_t)(k + 1) * m + k + 1;
+      const int c = c0 + lane;
+      double2 acc = make_double2(0.0, 0.0);
+      const int rend = min(q1, c0 + w);
+      for (int r0 = q0 + warp; r0 < rend; r0 += 4 * TD_WARPS) {
+        double2 a[4], vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + u * TD_WARPS;
+          const bool ok = r < rend && lane < w && c >= r;
+          a[u] = ok ? A[(size_t)r * m + c] : make_double2(0.0, 0.0);
+          vv[u] = r < rend ? v[r] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = cfma_conj(a[u], vv[u], acc);
+      }
+      acc_sh[warp][lane] = acc;
+      for (int qq = warp; qq < TD_STRIP; qq += TD_WARPS) {
+        double2 a2[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                         make_double2(0.0, 0.0)};
+        if (qq < w) {
+          const int cc = c0 + qq;
+          const double2* rowc = A + (size_t)cc * m;
+          for (int r0 = max(q0, cc + 1) + lane; r0 < q1; r0 += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int r = r0 + 32 * u;
+              if (r < q1) a2[u] = cfma(rowc[r], v[r], a2[u]);
+            }
+          }
+        }
+        const double2 a2s = warp_sum2(cadd(cadd(a2[0], a2[1]), cadd(a2[2], a2[3])));
+        if (lane == 0) pv_sh[0][qq] = a2s;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double2 p1 = make_double2(0.0, 0.0);
+        for (int wq = 0; wq < TD_WARPS; ++wq) p1 = cadd(p1, acc_sh[wq][lane]);
+        double2* hp = pan_hp(M) + (size_t)rem * 2 * TD_STRIP;
+        hp[lane] = p1;
+        hp[TD_STRIP + lane] = pv_sh[0][lane];
+      }
+      // partial dots of the panel corrections over this strip: w_i^+ v, v_i^+ v
+      if (q == 0 && threadIdx.x < 2 * j) {
+        const int i = threadIdx.x < j ? threadIdx.x : threadIdx.x - j;
+        const int col = threadIdx.x < j ? TD_NB + i : i;  // w_i first, then v_i
+        const double2* VW = pan_vw(M);
+        double2 t = make_double2(0.0, 0.0);
+        for (int qq = 0; qq < w; ++qq) t = cfma_conj(VW[(size_t)(k + 1 + c0 + qq) * 2 * TD_NB + col], v[c0 + qq], t);
+        pan_xy(M)[(size_t)sidx * 2 * TD_NB + threadIdx.x] = t;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(b.bar, target)) return;
+    // ---- phase 3: corrections, tau, the strip partials of p^+ v, and row k+1
     for (int item = blockIdx.x;; item += gridDim.x) {
       int rem = item, mi = -1;
       for (int i = 0; i < b.n; ++i) {
@@ -499,135 +636,72 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag(const __grid_constant__ 
       if (mi < 0) break;
       const EigMat& M = b.a[mi];
       const int m = M.m, n = m - k - 1;
+      const int ns = (n + TD_STRIP - 1) / TD_STRIP;
+      const int nq = (n + TD_CHUNK - 1) / TD_CHUNK;
       const int c0 = rem * TD_STRIP, w = min(TD_STRIP, n - c0);
       const double2* v = M.H + (size_t)k * m + k + 1;
-      const double2* A = M.H + (size_t)(k + 1) * m + k + 1;
-      const int c = c0 + lane;
-      double2 acc = make_double2(0.0, 0.0);
-      const int rmax = c0 + w;
-      for (int r0 = warp; r0 < rmax; r0 += 4 * TD_WARPS) {
-        double2 a[4], vv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = r0 + u * TD_WARPS;
-          const bool ok = r < rmax && lane < w && c >= r;
-          a[u] = ok ? A[(size_t)r * m + c] : make_double2(0.0, 0.0);
-          vv[u] = r < rmax ? v[r] : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc = cfma_conj(a[u], vv[u], acc);
-      }
-      acc_sh[warp][lane] = acc;
-      __syncthreads();
-      const double2 tau = M.tau[k];
-      for (int q = warp; q < w; q += TD_WARPS) {
-        const int cc = c0 + q;
-        double2 a2[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                         make_double2(0.0, 0.0)};
-        const double2* rowc = A + (size_t)cc * m;
-        for (int r0 = cc + 1 + lane; r0 < n; r0 += 128) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = r0 + 32 * u;
-            if (r < n) a2[u] = cfma(rowc[r], v[r], a2[u]);
-          }
-        }
-        const double2 a2s = warp_sum2(cadd(cadd(a2[0], a2[1]), cadd(a2[2], a2[3])));
-        if (lane == 0) {
-          double2 p1 = make_double2(0.0, 0.0);
-          for (int wq = 0; wq < TD_WARPS; ++wq) p1 = cadd(p1, acc_sh[wq][q]);
-          const double2 pc = cmul(tau, cadd(p1, a2s));
-          M.p[cc] = pc;
-          pd_sh[q] = cfma_conj(pc, v[cc], make_double2(0.0, 0.0));
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      // Row k+1 (the next pivot, if it is in this panel) is brought to A(k+1) here,
+      // spread over the strips, except for the alpha part of column k's term.
+      const bool nextrow = (k + 1 < k1);
+      if (threadIdx.x < 2 * j) {  // X_i = w_i^+ v, Y_i = v_i^+ v over the whole trailing set
+        const double2* xy = pan_xy(M);
         double2 t = make_double2(0.0, 0.0);
-        for (int q = 0; q < w; ++q) t = cadd(t, pd_sh[q]);
-        M.part[rem] = t;
-      }
-      __syncthreads();
-    }
-    if (!grid_sync(b.bar, target)) return;
-    // ---- phase W: w = p + alpha v once per element (alpha from the strip partials)
-    for (int item = blockIdx.x * blockDim.x + threadIdx.x;; item += gridDim.x * blockDim.x) {
-      int rem = item, mi = -1;
-      for (int i = 0; i < b.n; ++i) {
-        const int n = b.a[i].m - k - 1;
-        if (n <= 0) continue;
-        if (rem < n) { mi = i; break; }
-        rem -= n;
-      }
-      if (mi < 0) break;
-      const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1;
-      const double2 alpha = rank2_alpha(M, k, n);
-      M.pp[rem] = cfma(alpha, M.H[(size_t)k * m + k + 1 + rem], M.p[rem]);
-    }
-    if (!grid_sync(b.bar, target)) return;
-    // ---- phase R: A22 -= v w^+ + w v^+ on the upper triangle.  The first trailing row
-    // of every matrix goes to a whole block, which then builds the reflector of
-    // column k+1 from it (the critical path of the next column); rows >= 1 go to warps.
-    for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
-      const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1;
-      if (n <= 0) continue;
-      const double2* v = M.H + (size_t)k * m + k + 1;
-      const double2* wv = M.pp;
-      const double2 vr = v[0];
-      const double2 wr = wv[0];
-      double2* row = M.H + (size_t)(k + 1) * m + k + 1;
-      for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
-        const double2 vc = v[cc];
-        const double2 wc = wv[cc];
-        double2 a = row[cc];
-        a.x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc.x + wr.y * vc.y;
-        a.y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc.x - wr.x * vc.y;
-        row[cc] = a;
-      }
-      __syncthreads();
-      house_row_block(M, k + 1, red_sh, &scale_sh);
-    }
-    for (int item = gw;; item += nwarps) {
-      int rem = item, mi = -1;
-      for (int i = 0; i < b.n; ++i) {
-        const int n = b.a[i].m - k - 1;
-        if (n <= 1) continue;
-        if (rem < n - 1) { mi = i; break; }
-        rem -= n - 1;
-      }
-      if (mi < 0) break;
-      const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1, r = rem + 1;
-      const double2* v = M.H + (size_t)k * m + k + 1;
-      const double2* p = M.pp;  // w = p + alpha v
-      const double2 vr = v[r];
-      const double2 wr = p[r];
-      double2* row = M.H + (size_t)(k + 1 + r) * m + k + 1;
-      for (int c0 = r + lane; c0 < n; c0 += 128) {
-        double2 a[4], vc[4], pc[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int cc = c0 + 32 * u;
-          const bool ok = cc < n;
-          a[u] = ok ? row[cc] : make_double2(0.0, 0.0);
-          vc[u] = ok ? v[cc] : make_double2(0.0, 0.0);
-          pc[u] = ok ? p[cc] : make_double2(0.0, 0.0);
+        for (int s2 = 0; s2 < ns; ++s2) t = cadd(t, xy[(size_t)s2 * 2 * TD_NB + threadIdx.x]);
+        xy_sh[threadIdx.x] = t;
+        if (nextrow) {  // v_i(k+1) then w_i(k+1)
+          const int i = threadIdx.x < j ? threadIdx.x : TD_NB + threadIdx.x - j;
+          vk_sh[threadIdx.x] = pan_vw(M)[(size_t)(k + 1) * 2 * TD_NB + i];
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int cc = c0 + 32 * u;
-          if (cc < n) {
-            const double2 wc = pc[u];
-            a[u].x -= vr.x * wc.x + vr.y * wc.y + wr.x * vc[u].x + wr.y * vc[u].y;
-            a[u].y -= vr.y * wc.x - vr.x * wc.y + wr.y * vc[u].x - wr.x * vc[u].y;
-            row[cc] = a[u];
+      }
+      __syncthreads();
+      // warp wq adds the terms i = wq, wq + 8, ... for the 32 elements of the strip
+      double2 corr = make_double2(0.0, 0.0), rcorr = make_double2(0.0, 0.0);
+      if (lane < w) {
+        const double2* rc = pan_vw(M) + (size_t)(k + 1 + c0 + lane) * 2 * TD_NB;
+        for (int i = warp; i < j; i += TD_WARPS) {
+          const double2 vc = rc[i], wc = rc[TD_NB + i];
+          corr = cfma(vc, xy_sh[i], corr);      // v_i(c) (w_i^+ v)
+          corr = cfma(wc, xy_sh[j + i], corr);  // w_i(c) (v_i^+ v)
+          if (nextrow) {                        // v_i(k+1) conj(w_i(c)) + w_i(k+1) conj(v_i(c))
+            rcorr = cfma(vk_sh[i], cconj(wc), rcorr);
+            rcorr = cfma(vk_sh[j + i], cconj(vc), rcorr);
           }
         }
       }
+      pv_sh[warp][lane] = corr;
+      rv_sh[warp][lane] = rcorr;
+      __syncthreads();
+      if (warp == 0) {
+        double2 pd = make_double2(0.0, 0.0);
+        if (lane < w) {
+          double2 cs = make_double2(0.0, 0.0), rs = make_double2(0.0, 0.0);
+          for (int wq = 0; wq < TD_WARPS; ++wq) {
+            cs = cadd(cs, pv_sh[wq][lane]);
+            rs = cadd(rs, rv_sh[wq][lane]);
+          }
+          const double2* hp = pan_hp(M) + (size_t)rem * nq * 2 * TD_STRIP;
+          double2 h = make_double2(0.0, 0.0);
+          for (int q = 0; q < nq; ++q)
+            h = cadd(h, cadd(hp[(size_t)q * 2 * TD_STRIP + lane], hp[(size_t)q * 2 * TD_STRIP + TD_STRIP + lane]));
+          const double2 pc = cmul(M.tau[k], csub(h, cs));
+          M.p[c0 + lane] = pc;
+          pd = cfma_conj(pc, v[c0 + lane], make_double2(0.0, 0.0));
+          if (nextrow) {  // column k's term without alpha: conj(p(c)) (v_k(k+1) = 1)
+            double2* a = M.H + (size_t)(k + 1) * m + k + 1 + c0 + lane;
+            *a = csub(csub(*a, rs), cconj(pc));
+          }
+        }
+        pd = warp_sum2(pd);
+        if (lane == 0) M.part[rem] = pd;
+      }
+      __syncthreads();
     }
     if (!grid_sync(b.bar, target)) return;
+  }
+  // w of the panel's last column
+  for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
+    const EigMat& M = b.a[mi];
+    if (k1 - 1 < M.m - 1) finish_w(M, k1 - 1, k1 - 1 - k0, rank2_alpha(M, k1 - 1, M.m - k1));
   }
 }
 
@@ -647,7 +721,7 @@ int eig_trace(const EigBatch& b, cudaStream_t s) {
   return 1;
 }
 
-int eig_tridiagonalize(const EigBatch& b, cudaStream_t s) {
+int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* status, cudaStream_t s) {
   if (b.n == 0) return 0;
   const int mm = max_m(b);
   static int grid = 0;
@@ -655,15 +729,57 @@ int eig_tridiagonalize(const EigBatch& b, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, TD_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_panel, TD_THREADS, 0);
     grid = std::max(1, sms * std::min(per_sm, 2));
   }
-  int mmax = mm;
-  cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
-  void* args[] = {const_cast<EigBatch*>(&b), &mmax};
-  if (cudaLaunchCooperativeKernel((const void*)k_tridiag, dim3(grid), dim3(TD_THREADS), args, 0, s) != cudaSuccess)
-    return -1;
-  return 1;
+  int launches = 0;
+  for (int k0 = 0; k0 < mm; k0 += TD_NB) {
+    int k1 = std::min(mm, k0 + TD_NB);
+    cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
+    void* args[] = {const_cast<EigBatch*>(&b), &k0, &k1};
+    if (cudaLaunchCooperativeKernel((const void*)k_tridiag_panel, dim3(grid), dim3(TD_THREADS), args, 0, s) !=
+        cudaSuccess)
+      return -1;
+    ++launches;
+    // trailing update A[k1:, k1:] -= V W^+ + W V^+ (Hermitian, lower tiles mirrored)
+    Gemm g(true, OP_N, OP_C);
+    std::vector<OzProb> oz;
+    for (int i = 0; i < b.n; ++i) {
+      const EigMat& M = b.a[i];
+      const int n = M.m - k1;
+      if (n <= 0) continue;
+      double2* C = M.H + (size_t)k1 * M.m + k1;
+      const double2* VW = M.pan + (size_t)k1 * 2 * TD_NB;
+      const double2* WV = M.pan + (size_t)M.m * 2 * TD_NB + (size_t)k1 * 2 * TD_NB;
+      if (mixed) {
+        OzProb q{};
+        q.a = OzOperand{VW, 2 * TD_NB, 1, nullptr, 1, 0};
+        q.b = OzOperand{WV, 2 * TD_NB, 1, nullptr, 1, 1};
+        q.M = q.N = n;
+        q.K = 2 * TD_NB;
+        q.C = C;
+        q.ldc = M.m;
+        q.alpha = -1.0;
+        q.beta = 1;
+        q.row_div = q.col_div = 1;
+        q.herm = 1;
+        q.ws = oz_ws[i];
+        oz.push_back(q);
+      } else {
+        GemmProb& p = g.add(n, n, 2 * TD_NB, VW, 2 * TD_NB, WV, 2 * TD_NB, C, M.m);
+        p.alpha_re = -1.0;
+        p.accumulate = 1;
+        p.herm = 1;
+      }
+    }
+    launches += mixed ? oz_gemm_launch(oz, status, s) : g.launch(s);
+  }
+  return launches;
+}
+
+size_t eig_panel_doubles2(int m) {
+  const size_t slabs = (size_t)((m + TD_STRIP - 1) / TD_STRIP) * ((m + TD_CHUNK - 1) / TD_CHUNK);
+  return (size_t)m * 4 * TD_NB + (size_t)EIG_PARTS * 2 * TD_NB + slabs * 2 * TD_STRIP;
 }
 
 int eig_bisect(const EigBatch& b, cudaStream_t s) {

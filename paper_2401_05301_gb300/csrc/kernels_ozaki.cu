@@ -499,19 +499,25 @@ __global__ void __launch_bounds__(OZ_NT, 1) k_oz_gemm(const __grid_constant__ Oz
         double f = P.alpha;
         if (P.s_row) f *= P.s_row[i / P.row_div];
         if (P.s_col) f *= P.s_col[jj / P.col_div];
-        P.C[(long long)i * P.ldc + jj] = make_double2(stage[r * OZ_STAGE_LD + cc] * f,
-                                                      stage[r * OZ_STAGE_LD + OZ_TNC + cc] * f);
+        double2* dst = P.C + (long long)i * P.ldc + jj;
+        double2 val = make_double2(stage[r * OZ_STAGE_LD + cc] * f, stage[r * OZ_STAGE_LD + OZ_TNC + cc] * f);
+        if (P.beta) {
+          const double2 old = *dst;
+          val.x += old.x;
+          val.y += old.y;
+        }
+        *dst = val;
+        stage[r * OZ_STAGE_LD + cc] = val.x;  // the final value, for the mirror below
+        stage[r * OZ_STAGE_LD + OZ_TNC + cc] = val.y;
       }
       if (P.herm) {  // mirror the strictly lower part: C[j][i] = conj(C[i][j])
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * OZ_DW) : "memory");
         for (int e = tid; e < OZ_TM * OZ_TNC; e += 32 * OZ_DW) {
           const int cc = e / OZ_TM, r = e % OZ_TM;
           const int i = mt * OZ_TM + r, jj = nt * OZ_TNC + cc;
           if (i >= P.M || jj >= P.N || jj >= i) continue;
-          double f = P.alpha;
-          if (P.s_row) f *= P.s_row[i / P.row_div];
-          if (P.s_col) f *= P.s_col[jj / P.col_div];
-          P.C[(long long)jj * P.ldc + i] = make_double2(stage[r * OZ_STAGE_LD + cc] * f,
-                                                        -(stage[r * OZ_STAGE_LD + OZ_TNC + cc] * f));
+          P.C[(long long)jj * P.ldc + i] =
+              make_double2(stage[r * OZ_STAGE_LD + cc], -stage[r * OZ_STAGE_LD + OZ_TNC + cc]);
         }
       }
     }
@@ -609,7 +615,7 @@ int oz_gemm_launch(const std::vector<OzProb>& probs, int* status, cudaStream_t s
       t.DA = DA; t.D1 = gram ? DA : D1; t.D2 = D2; t.eA = eA; t.eB = eB;
       t.C = p.C; t.ldc = p.ldc; t.alpha = p.alpha; t.s_row = p.s_row; t.s_col = p.s_col;
       t.row_div = std::max(1, p.row_div); t.col_div = std::max(1, p.col_div);
-      t.M = p.M; t.N = p.N; t.nkt = g.nkt; t.nrbA = g.nrbA; t.nrbB = g.nrbB; t.herm = p.herm;
+      t.M = p.M; t.N = p.N; t.nkt = g.nkt; t.nrbA = g.nrbA; t.nrbB = g.nrbB; t.herm = p.herm; t.beta = p.beta;
       t.tiles_n = (p.N + OZ_TNC - 1) / OZ_TNC;
       const int tm = (p.M + OZ_TM - 1) / OZ_TM;
       int nt_tiles = 0;

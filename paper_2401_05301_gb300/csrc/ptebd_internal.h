@@ -83,8 +83,9 @@ struct OzProb {
   const double* s_row;
   const double* s_col;
   int row_div, col_div;
-  int herm;  // Hermitian result: only j <= i is computed, then mirrored (needs gram)
+  int herm;  // Hermitian result (M == N): only j <= i is computed, then mirrored
   int gram;  // b(j, k) = conj(a(j, k)), N = M: the digits of a serve both operands
+  int beta;  // 1: C += result (for herm, the lower triangle is read), 0: C = result
   void* ws;  // oz_workspace_bytes(M, N, K, gram) bytes, 256-byte aligned, owned by the caller
 };
 constexpr int OZ_MAXP = 16;
@@ -114,7 +115,7 @@ struct OzTile {
   double alpha;
   const double* s_row;
   const double* s_col;
-  int row_div, col_div, M, N, nkt, nrbA, nrbB, herm, tiles_n;
+  int row_div, col_div, M, N, nkt, nrbA, nrbB, herm, tiles_n, beta;
 };
 struct OzGemmBatch {
   OzTile p[OZ_MAXP];
@@ -155,7 +156,6 @@ struct EigMat {
   double2* tau;      // Householder scalars [m]
   double2* part;     // partial dot products [EIG_PARTS], one per 32-column strip
   double2* p;        // p = tau A22 v [m]
-  double2* pp;       // w = p + alpha v of the current column [m]
   double* evals;     // eigenvalues, descending [kmax]
   double* trace;     // [1] trace of H (sum of Re H_rr), taken before reduction
   double* Z;         // m x K real eigenvectors of T (row-major, ld = K)
@@ -163,6 +163,7 @@ struct EigMat {
   double* S;         // K x K scratch
   double* work;      // inverse-iteration LU scratch, 5 * m * K doubles
   double2* U;        // K x m eigenvectors of H, one per row (U[j*m + r] = u_j[r])
+  double2* pan;      // panel arrays of the blocked reduction [eig_panel_doubles2(m)]
   int m, kmax, K;
 };
 
@@ -176,9 +177,13 @@ constexpr int EIG_PARTS = 384;  // partial sums of p^+ v, one per strip of 32 co
 
 // Each returns the number of kernel launches issued.
 int eig_trace(const EigBatch& b, cudaStream_t s);
-// One cooperative launch; returns -1 if the launch is refused.  A barrier that
-// times out sets b.bar[2] (checked by the caller after synchronising).
-int eig_tridiagonalize(const EigBatch& b, cudaStream_t s);
+// Blocked (panels of 32 columns): one cooperative launch per panel plus the
+// trailing rank-64 update, on the exact-digit tensor-core engine when mixed
+// (oz_ws[i]: a digit workspace per matrix) or the FP64 GEMM otherwise.
+// Returns the launches issued, or -1 if a cooperative launch is refused.  A
+// barrier that times out sets b.bar[2] (checked by the caller after synchronising).
+int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* status, cudaStream_t s);
+size_t eig_panel_doubles2(int m);  // complex elements of EigMat::pan for an m x m matrix
 int eig_bisect(const EigBatch& b, cudaStream_t s);
 // Inverse iteration on T for eigenvalues 0..K-1, Newton-Schulz orthonormalisation,
 // and back-transformation U = Q Z.  Reads a[i].K (set from the eigenvalues).
