@@ -378,7 +378,7 @@ constexpr int TD_THREADS = 256;
 constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
 constexpr int TD_NB = 32;      // columns per panel of the blocked reduction
-constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian product
+constexpr int TD_CHUNK = 128;  // trailing indices per slab of the Hermitian product
 
 
 // Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
@@ -462,11 +462,15 @@ __device__ void house_row_block(const EigMat& M, int k, double* sh, double2* sca
   __syncthreads();
 }
 
-// alpha = -tau (p^+ v) / 2 from the per-strip partial sums (fixed order)
+// alpha = -tau (p^+ v) / 2 from the per-strip partial sums (fixed order): every
+// warp forms the sum with its lanes striding the partials, so no thread runs a
+// long dependent chain of loads.
 __device__ __forceinline__ double2 rank2_alpha(const EigMat& M, int k, int n) {
   const int ns = (n + TD_STRIP - 1) / TD_STRIP;
+  const int lane = threadIdx.x & 31;
   double2 dot = make_double2(0.0, 0.0);
-  for (int j = 0; j < ns; ++j) dot = cadd(dot, M.part[j]);
+  for (int j = lane; j < ns; j += 32) dot = cadd(dot, M.part[j]);
+  dot = warp_sum2(dot);
   const double2 t2 = cmul(M.tau[k], dot);
   return make_double2(-0.5 * t2.x, -0.5 * t2.y);
 }
@@ -643,12 +647,15 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
       // Row k+1 (the next pivot, if it is in this panel) is brought to A(k+1) here,
       // spread over the strips, except for the alpha part of column k's term.
       const bool nextrow = (k + 1 < k1);
-      if (threadIdx.x < 2 * j) {  // X_i = w_i^+ v, Y_i = v_i^+ v over the whole trailing set
+      {  // X_i = w_i^+ v, Y_i = v_i^+ v over the whole trailing set: warp per value, lanes over strips
         const double2* xy = pan_xy(M);
-        double2 t = make_double2(0.0, 0.0);
-        for (int s2 = 0; s2 < ns; ++s2) t = cadd(t, xy[(size_t)s2 * 2 * TD_NB + threadIdx.x]);
-        xy_sh[threadIdx.x] = t;
-        if (nextrow) {  // v_i(k+1) then w_i(k+1)
+        for (int t = warp; t < 2 * j; t += TD_WARPS) {
+          double2 acc2 = make_double2(0.0, 0.0);
+          for (int s2 = lane; s2 < ns; s2 += 32) acc2 = cadd(acc2, xy[(size_t)s2 * 2 * TD_NB + t]);
+          acc2 = warp_sum2(acc2);
+          if (lane == 0) xy_sh[t] = acc2;
+        }
+        if (nextrow && threadIdx.x < 2 * j) {  // v_i(k+1) then w_i(k+1)
           const int i = threadIdx.x < j ? threadIdx.x : TD_NB + threadIdx.x - j;
           vk_sh[threadIdx.x] = pan_vw(M)[(size_t)(k + 1) * 2 * TD_NB + i];
         }
