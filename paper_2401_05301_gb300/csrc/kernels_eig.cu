@@ -378,7 +378,7 @@ constexpr int TD_THREADS = 256;
 constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
 constexpr int TD_NB = 32;      // columns per panel of the blocked reduction
-constexpr int TD_CHUNK = 128;  // trailing indices per slab of the Hermitian product
+constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian product
 
 
 // Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
@@ -647,15 +647,13 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
       // Row k+1 (the next pivot, if it is in this panel) is brought to A(k+1) here,
       // spread over the strips, except for the alpha part of column k's term.
       const bool nextrow = (k + 1 < k1);
-      {  // X_i = w_i^+ v, Y_i = v_i^+ v over the whole trailing set: warp per value, lanes over strips
+      if (threadIdx.x < 2 * j) {  // X_i = w_i^+ v, Y_i = v_i^+ v over the whole trailing set
         const double2* xy = pan_xy(M);
-        for (int t = warp; t < 2 * j; t += TD_WARPS) {
-          double2 acc2 = make_double2(0.0, 0.0);
-          for (int s2 = lane; s2 < ns; s2 += 32) acc2 = cadd(acc2, xy[(size_t)s2 * 2 * TD_NB + t]);
-          acc2 = warp_sum2(acc2);
-          if (lane == 0) xy_sh[t] = acc2;
-        }
-        if (nextrow && threadIdx.x < 2 * j) {  // v_i(k+1) then w_i(k+1)
+        double2 t = make_double2(0.0, 0.0);
+#pragma unroll 4
+        for (int s2 = 0; s2 < ns; ++s2) t = cadd(t, xy[(size_t)s2 * 2 * TD_NB + threadIdx.x]);
+        xy_sh[threadIdx.x] = t;
+        if (nextrow) {  // v_i(k+1) then w_i(k+1)
           const int i = threadIdx.x < j ? threadIdx.x : TD_NB + threadIdx.x - j;
           vk_sh[threadIdx.x] = pan_vw(M)[(size_t)(k + 1) * 2 * TD_NB + i];
         }
