@@ -405,7 +405,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
       w += 8.0 * m * m * K + 12.0 * m * K * K;
     }
     ProfScope ps(c, TEBD_PROF_EIGVEC, w);
-    c->launches += eig_vectors(eb, c->stream);
+    c->launches += eig_vectors(eb, c->precision == 1, oz_ws, c->d_status, c->stream);
   }
   for (size_t t = 0; t < ts.size(); ++t) {
     const EigMat& M = eb.a[t];

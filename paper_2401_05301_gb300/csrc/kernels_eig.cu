@@ -311,56 +311,73 @@ __global__ void k_z_to_u(const __grid_constant__ EigBatch b, int use_z2) {
   }
 }
 
-constexpr int CPB = 8;  // eigenvectors per block in the back-transformation
+// ---- blocked back-transformation ----------------------------------------------------------
+// U <- Q Z with Q = H(0) H(1) ... H(m-2) is applied as blocks of BT reflectors,
+// Q_p = H(k0) ... H(k0+BT-1) = I - V T V^+ (compact WY form, T upper triangular:
+// T[i][i] = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] (V^+ V)[0:i, i]), last block first:
+// U^T <- U^T - V T (V^+ U^T), i.e. three matrix products per block on the rows of U.
+constexpr int BT = 64;  // reflectors per block
 
-// U <- H(0) H(1) ... H(m-2) U, one block per CPB eigenvectors; per reflector the
-// CPB dot products v^+ u are reduced together (one round of barriers).
-__global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ EigBatch b) {
+__host__ __device__ inline size_t bt_offset(int m) {
+  const size_t slabs = (size_t)((m + 31) / 32) * ((m + 255) / 256);
+  return (size_t)m * 128 + (size_t)EIG_PARTS * 64 + slabs * 64;
+}
+// V (m x BT) and conj(V) reuse the panel arrays; then G = V^+ V, T^T, S = U conj(V), S T^T.
+__device__ __forceinline__ double2* bt_V(const EigMat& M) { return M.pan; }
+__device__ __forceinline__ double2* bt_Vc(const EigMat& M) { return M.pan + (size_t)M.m * BT; }
+__device__ __forceinline__ double2* bt_G(const EigMat& M) { return M.pan + bt_offset(M.m); }
+__device__ __forceinline__ double2* bt_Tt(const EigMat& M) { return bt_G(M) + BT * BT; }
+
+// Column i of V = v_{k0+i} (unit entry at row k0+i+1, zero above), from the rows of H.
+__global__ void k_bt_prep(const __grid_constant__ EigBatch b, int k0) {
   const EigMat& M = b.a[blockIdx.y];
-  const int m = M.m, K = M.K;
-  const int c0 = blockIdx.x * CPB;
-  if (c0 >= K) return;
-  const int ncol = min(CPB, K - c0);
-  __shared__ double2 red[NT / 32][CPB];
-  __shared__ double2 wsh[CPB];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = m - 2; k >= 0; --k) {
-    const double2 tau = M.tau[k];
-    if (tau.x == 0.0 && tau.y == 0.0) continue;
-    const int n = m - k - 1;
-    const double2* v = M.H + (size_t)k * m + k + 1;
-    double2 acc[CPB];
-#pragma unroll
-    for (int cc = 0; cc < CPB; ++cc) acc[cc] = make_double2(0.0, 0.0);
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const double2 vr = v[r];
-#pragma unroll
-      for (int cc = 0; cc < CPB; ++cc)
-        if (cc < ncol) acc[cc] = cfma_conj(vr, M.U[(size_t)(c0 + cc) * m + k + 1 + r], acc[cc]);
+  const int m = M.m;
+  if (M.K == 0 || k0 >= m - 1) return;
+  double2* V = bt_V(M);
+  double2* Vc = bt_Vc(M);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * BT; idx += gridDim.x * blockDim.x) {
+    const int r = idx / BT, i = idx % BT, k = k0 + i;
+    double2 v = make_double2(0.0, 0.0);
+    if (k < m - 1) {
+      if (r == k + 1) v = make_double2(1.0, 0.0);
+      else if (r > k + 1) v = M.H[(size_t)k * m + r];
     }
-#pragma unroll
-    for (int cc = 0; cc < CPB; ++cc) {
-      const double2 t = warp_sum2(acc[cc]);
-      if (lane == 0) red[warp][cc] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < CPB) {
-      double2 t = make_double2(0.0, 0.0);
-      for (int w = 0; w < NT / 32; ++w) t = cadd(t, red[w][threadIdx.x]);
-      wsh[threadIdx.x] = cmul(tau, t);
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const double2 vr = v[r];
-#pragma unroll
-      for (int cc = 0; cc < CPB; ++cc) {
-        if (cc < ncol) {
-          double2* u = M.U + (size_t)(c0 + cc) * m + k + 1 + r;
-          *u = csub(*u, cmul(vr, wsh[cc]));
-        }
-      }
+    V[idx] = v;
+    Vc[idx] = cconj(v);
+  }
+}
+
+// T of the block from G = V^+ V and tau (one block per matrix; four threads per
+// row of T share each column's sum), written transposed.
+__global__ void __launch_bounds__(4 * BT) k_bt_T(const __grid_constant__ EigBatch b, int k0) {
+  const EigMat& M = b.a[blockIdx.x];
+  const int m = M.m;
+  if (M.K == 0 || k0 >= m - 1) return;
+  const int nb = min(BT, m - 1 - k0);
+  extern __shared__ double2 Tsh[];  // BT x (BT + 1)
+  const double2* G = bt_G(M);
+  for (int idx = threadIdx.x; idx < BT * (BT + 1); idx += blockDim.x) Tsh[idx] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const int l = threadIdx.x >> 2, part = threadIdx.x & 3;
+  for (int i = 0; i < nb; ++i) {
+    const double2 ti = M.tau[k0 + i];
+    double2 acc = make_double2(0.0, 0.0);
+    if (l < i)
+      for (int q = l + part; q < i; q += 4) acc = cfma(Tsh[l * (BT + 1) + q], G[q * BT + i], acc);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+    if (part == 0) {
+      if (l < i) Tsh[l * (BT + 1) + i] = make_double2(-(ti.x * acc.x - ti.y * acc.y), -(ti.x * acc.y + ti.y * acc.x));
+      else if (l == i) Tsh[l * (BT + 1) + i] = ti;
     }
     __syncthreads();
+  }
+  double2* Tt = bt_Tt(M);
+  for (int idx = threadIdx.x; idx < BT * BT; idx += blockDim.x) {
+    const int r = idx / BT, c = idx % BT;  // Tt[r][c] = T[c][r]
+    Tt[idx] = Tsh[c * (BT + 1) + r];
   }
 }
 
@@ -783,9 +800,10 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
 }
 
 size_t eig_panel_doubles2(int m) {
-  const size_t slabs = (size_t)((m + TD_STRIP - 1) / TD_STRIP) * ((m + TD_CHUNK - 1) / TD_CHUNK);
-  return (size_t)m * 4 * TD_NB + (size_t)EIG_PARTS * 2 * TD_NB + slabs * 2 * TD_STRIP;
+  // panel arrays, then the back-transformation's G, T^T, S and S T^T
+  return bt_offset(m) + 2 * BT * BT + (size_t)2 * m * BT;
 }
+static_assert(BT == 2 * TD_NB && TD_STRIP == 32 && TD_CHUNK == 256, "bt_offset() mirrors the panel layout");
 
 int eig_bisect(const EigBatch& b, cudaStream_t s) {
   if (b.n == 0) return 0;
@@ -796,7 +814,7 @@ int eig_bisect(const EigBatch& b, cudaStream_t s) {
   return 1;
 }
 
-int eig_vectors(const EigBatch& b0, cudaStream_t s) {
+int eig_vectors(const EigBatch& b0, bool mixed, void* const* oz_ws, int* status, cudaStream_t s) {
   if (b0.n == 0) return 0;
   EigBatch b = b0;
   int Kmax = 0, launches = 0;
@@ -830,8 +848,69 @@ int eig_vectors(const EigBatch& b0, cudaStream_t s) {
   const int mm = max_m(b);
   k_z_to_u<<<dim3((mm + 31) / 32, (Kmax + 31) / 32, b.n), dim3(32, 8), 0, s>>>(b, in_z2 ? 1 : 0);
   ++launches;
-  k_backtransform<<<dim3((Kmax + CPB - 1) / CPB, b.n), NT, 0, s>>>(b);
-  ++launches;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_bt_T, cudaFuncAttributeMaxDynamicSharedMemorySize, BT * (BT + 1) * 16);
+    attr = true;
+  }
+  const int nblk = (mm - 1 + BT - 1) / BT;
+  for (int p = nblk - 1; p >= 0; --p) {
+    const int k0 = p * BT;
+    k_bt_prep<<<dim3(64, b.n), 256, 0, s>>>(b, k0);
+    ++launches;
+    std::vector<OzProb> oG, oS, oS2, oU;
+    Gemm gG(true, OP_C, OP_N), gS(true, OP_N, OP_CJ), gS2(true, OP_N, OP_N), gU(true, OP_N, OP_C);
+    for (int i = 0; i < b.n; ++i) {
+      const EigMat& M = b.a[i];
+      const int m = M.m, K = M.K, mr = m - k0 - 1;
+      if (K == 0 || mr <= 0) continue;
+      const double2* V = M.pan + (size_t)(k0 + 1) * BT;
+      const double2* Vc = M.pan + (size_t)m * BT + (size_t)(k0 + 1) * BT;
+      double2* G = M.pan + bt_offset(m);
+      double2* Tt = G + BT * BT;
+      double2* S = Tt + BT * BT;
+      double2* S2 = S + (size_t)m * BT;
+      double2* U = M.U + k0 + 1;
+      if (mixed) {
+        OzProb q{};
+        q.row_div = q.col_div = 1;
+        q.alpha = 1.0;
+        q.ws = oz_ws[i];
+        OzProb g = q;  // G = V^+ V
+        g.a = OzOperand{V, 1, BT, nullptr, 1, 1};
+        g.M = g.N = BT; g.K = mr; g.C = G; g.ldc = BT; g.gram = g.herm = 1;
+        oG.push_back(g);
+        OzProb t = q;  // S = U conj(V): S[j][i] = sum_r U[j][r] conj(V[r][i])
+        t.a = OzOperand{U, m, 1, nullptr, 1, 0};
+        t.b = OzOperand{V, 1, BT, nullptr, 1, 1};
+        t.M = K; t.N = BT; t.K = mr; t.C = S; t.ldc = BT;
+        oS.push_back(t);
+        OzProb t2 = q;  // S2 = S T^T
+        t2.a = OzOperand{S, BT, 1, nullptr, 1, 0};
+        t2.b = OzOperand{Tt, 1, BT, nullptr, 1, 0};
+        t2.M = K; t2.N = BT; t2.K = BT; t2.C = S2; t2.ldc = BT;
+        oS2.push_back(t2);
+        OzProb u = q;  // U -= S2 V^T
+        u.a = OzOperand{S2, BT, 1, nullptr, 1, 0};
+        u.b = OzOperand{V, BT, 1, nullptr, 1, 0};
+        u.M = K; u.N = mr; u.K = BT; u.C = U; u.ldc = m; u.alpha = -1.0; u.beta = 1;
+        oU.push_back(u);
+      } else {
+        gG.add(BT, BT, mr, V, BT, V, BT, G, BT);
+        gS.add(K, BT, mr, U, m, V, BT, S, BT);
+        gS2.add(K, BT, BT, S, BT, Tt, BT, S2, BT);
+        GemmProb& pu = gU.add(K, mr, BT, S2, BT, Vc, BT, U, m);
+        pu.alpha_re = -1.0;
+        pu.accumulate = 1;
+      }
+    }
+    launches += mixed ? oz_gemm_launch(oG, status, s) : gG.launch(s);
+    k_bt_T<<<b.n, 4 * BT, BT * (BT + 1) * 16, s>>>(b, k0);
+    ++launches;
+    launches += mixed ? oz_gemm_launch(oS, status, s) : gS.launch(s);
+    launches += mixed ? oz_gemm_launch(oS2, status, s) : gS2.launch(s);
+    launches += mixed ? oz_gemm_launch(oU, status, s) : gU.launch(s);
+  }
   return launches;
 }
 
