@@ -508,6 +508,59 @@ OzProb oz_project(const double2* U, int K, int m, const double* lam, int d, cons
   return q;
 }
 
+// One Newton-Schulz polar step on the rows of the kept right singular vectors,
+// V <- (3I - V V^+) V / 2.  Rows formed as u_k^+ theta' / s_k carry overlaps of
+// order eps s_1 / s_k with the leading rows; the canonical-form observables and
+// the next updates assume orthonormal rows, so the overlaps are removed (the
+// step squares the error: from ~1e-10 to rounding).  Scratch: the slot's Gram
+// buffer (rows x rows) and Th (rows x n).  second: V2 = B_{i+2}, else V1^+.
+int reorthonormalise(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
+  cudaStream_t s = c->stream;
+  const bool mixed = c->precision == 1;
+  Gemm gG(true, OP_N, OP_C), gA(true, OP_N, OP_N);
+  std::vector<OzProb> oG, oA;
+  std::vector<PolarArgs> pa;
+  double w = 0.0;
+  for (auto& T : ts) {
+    const Slot& S = T.h->slots[T.slot];
+    double2* V = second ? T.h->B[T.i + 2] : S.V1h;
+    const int rows = second ? T.chi2 : T.chi1, n = second ? T.n2 : T.n1;
+    if (rows <= 0 || n <= 0) continue;
+    if (mixed) {
+      OzProb g{};
+      g.a = OzOperand{V, n, 1, nullptr, 1, 0};
+      g.M = g.N = rows; g.K = n; g.C = S.H; g.ldc = rows; g.alpha = 1.0;
+      g.row_div = g.col_div = 1; g.gram = g.herm = 1; g.ws = S.oz;
+      oG.push_back(g);
+      OzProb a{};
+      a.a = OzOperand{S.H, rows, 1, nullptr, 1, 0};
+      a.b = OzOperand{V, 1, n, nullptr, 1, 0};
+      a.M = rows; a.N = n; a.K = rows; a.C = S.Th; a.ldc = n; a.alpha = 1.0;
+      a.row_div = a.col_div = 1; a.ws = S.oz;
+      oA.push_back(a);
+    } else {
+      GemmProb& g = gG.add(rows, rows, n, V, n, V, n, S.H, rows);
+      g.herm = 1;
+      gA.add(rows, n, rows, S.H, rows, V, n, S.Th, n);
+    }
+    pa.push_back(PolarArgs{S.H, rows});
+    w += 12.0 * (double)rows * rows * n;
+  }
+  ProfScope ps(c, TEBD_PROF_PROJECT, w);
+  c->launches += mixed ? oz_gemm_launch(oG, c->d_status, s) : gG.launch(s);
+  c->launches += launch_polar_form(pa.data(), (int)pa.size(), s);
+  c->launches += mixed ? oz_gemm_launch(oA, c->d_status, s) : gA.launch(s);
+  for (auto& T : ts) {
+    const Slot& S = T.h->slots[T.slot];
+    double2* V = second ? T.h->B[T.i + 2] : S.V1h;
+    const int rows = second ? T.chi2 : T.chi1, n = second ? T.n2 : T.n1;
+    if (rows <= 0 || n <= 0) continue;
+    if (cudaMemcpyAsync(V, S.Th, sizeof(double2) * rows * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail_cuda(c);
+  }
+  return check_launch(c);
+}
+
 // One batch of independent local updates (disjoint triples, possibly of
 // different simulations), driven on c's stream.  c->precision selects the
 // contraction path for the whole batch.
@@ -598,6 +651,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
       c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
     }
+    if (int r = reorthonormalise(c, ts, false)) return r;
     // B_i = C V1 / ||s||;  Gram H2 = (lam' V1^+)(lam' V1^+)^+ viewed as (chi' d) x (d chr)
     Gemm g6(true, OP_N, OP_C), g7(true, OP_N, OP_C);
     std::vector<OzProb> oz7;
@@ -657,6 +711,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       ProfScope ps(c, TEBD_PROF_TRUNCATE, 0.0);
       c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
     }
+    if (int r = reorthonormalise(c, ts, true)) return r;
     // B_{i+1} = V1^+ V2 / ||s2||,  B_{i+2} = V2^+ (gathered above)
     Gemm g9(true, OP_N, OP_C);
     for (auto& T : ts) {

@@ -243,6 +243,37 @@ int launch_truncate(const TruncBatch& b, cudaStream_t s) {
   return 1;
 }
 
+namespace {
+struct PolarBatch {
+  PolarArgs a[TRUNC_MAXP];
+  int n;
+};
+__global__ void k_polar_form(const __grid_constant__ PolarBatch pb) {
+  const PolarArgs& a = pb.a[blockIdx.y];
+  const int nn = a.n * a.n;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nn; idx += gridDim.x * blockDim.x) {
+    const double2 g = a.G[idx];
+    a.G[idx] = make_double2((idx / a.n == idx % a.n ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+  }
+}
+}  // namespace
+
+int launch_polar_form(const PolarArgs* a, int n, cudaStream_t s) {
+  int launches = 0;
+  for (int i0 = 0; i0 < n; i0 += TRUNC_MAXP) {
+    PolarBatch pb{};
+    int nmax = 0;
+    for (int i = i0; i < std::min(n, i0 + TRUNC_MAXP); ++i) {
+      pb.a[pb.n++] = a[i];
+      nmax = std::max(nmax, a[i].n);
+    }
+    if (nmax == 0) continue;
+    k_polar_form<<<dim3(std::min(64, (nmax * nmax + 255) / 256), pb.n), 256, 0, s>>>(pb);
+    ++launches;
+  }
+  return launches;
+}
+
 int launch_gather_rows(const GatherArgs* a, int n, cudaStream_t s) {
   int launches = 0;
   for (int i0 = 0; i0 < n; i0 += TRUNC_MAXP) {

@@ -223,6 +223,13 @@ struct GatherArgs {
 };
 int launch_gather_rows(const GatherArgs* a, int n, cudaStream_t s);
 
+// G <- 3/2 I - 1/2 G for square complex matrices (the Newton-Schulz polar step).
+struct PolarArgs {
+  double2* G;
+  int n;
+};
+int launch_polar_form(const PolarArgs* a, int n, cudaStream_t s);
+
 int launch_init_product(double2* const* B, double* const* lam, const int* occ_dev, int L, int d,
                         cudaStream_t s);
 
