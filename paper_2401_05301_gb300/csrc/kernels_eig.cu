@@ -135,17 +135,17 @@ __device__ void gershgorin(const double* d, const double* e, int m, double* sh, 
   gu = -block_min(hi, sh);
 }
 
-// Multisection: one warp per eigenvalue; each iteration the 32 lanes count
-// the eigenvalues below 32 interior points of the current interval, which
-// shrinks it 33-fold (about 11 iterations to machine precision instead of 52).
+// Bisection, one thread per eigenvalue.  With hundreds of eigenvalues per matrix
+// the stage is bound by FP64 throughput, not by its serial recurrences, so plain
+// halving (one Sturm count per step, ~52 steps) beats multisection (32 counts per
+// step, ~11 steps): about 7x fewer FP64 operations.
 __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   const EigMat& M = b.a[blockIdx.y];
   const int m = M.m;
   __shared__ double sh[33];
   double gl, gu;
   gershgorin(M.d, M.e, m, sh, gl, gu);
-  const int lane = threadIdx.x & 31;
-  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M.kmax || j >= m) return;
   const double bnorm = fmax(fabs(gl), fabs(gu));
   const double eps = DBL_EPSILON, tiny = DBL_MIN * fmax(1.0, bnorm * bnorm);
@@ -153,17 +153,13 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   double hi = gu + 2.0 * eps * bnorm * m + 4.0 * tiny;
   const double atol = 2.0 * eps * bnorm + 4.0 * tiny;
   const int target = m - 1 - j;  // ascending index of the j-th largest
-  for (int it = 0; it < 40 && hi - lo > atol; ++it) {
-    const double x = lo + (hi - lo) * (double)(lane + 1) * (1.0 / 33.0);
-    const bool above = sturm_count(M.d, M.e, m, x) > target;  // eigenvalue lies below x
-    const unsigned ball = __ballot_sync(0xffffffffu, above);
-    const int l0 = ball ? (__ffs(ball) - 1) : 32;  // first point above the eigenvalue (32: none)
-    const double xa = __shfl_sync(0xffffffffu, x, l0 > 0 ? l0 - 1 : 0);
-    const double xb = __shfl_sync(0xffffffffu, x, l0 < 32 ? l0 : 31);
-    if (l0 > 0) lo = xa;
-    if (l0 < 32) hi = xb;
+  for (int it = 0; it < 128 && hi - lo > atol; ++it) {
+    const double x = 0.5 * (lo + hi);
+    if (x <= lo || x >= hi) break;  // interval at the resolution of the doubles
+    if (sturm_count(M.d, M.e, m, x) > target) hi = x;  // eigenvalue lies below x
+    else lo = x;
   }
-  if (lane == 0) M.evals[j] = 0.5 * (lo + hi);
+  M.evals[j] = 0.5 * (lo + hi);
 }
 
 // ---- inverse iteration ----------------------------------------------------------------
@@ -308,6 +304,60 @@ __global__ void k_z_to_u(const __grid_constant__ EigBatch b, int use_z2) {
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (c < K && r < m) M.U[(size_t)c * m + r] = make_double2(tile[threadIdx.x][i], 0.0);
+  }
+}
+
+constexpr int CPB = 8;  // eigenvectors per block in the back-transformation
+
+// FP64 path: U <- H(0) H(1) ... H(m-2) U reflector by reflector, one block per CPB
+// eigenvectors; per reflector the CPB dot products v^+ u are reduced together.
+// (On FP64 CUDA cores this keeps more blocks busy than the blocked form's thin products.)
+__global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  const int m = M.m, K = M.K;
+  const int c0 = blockIdx.x * CPB;
+  if (c0 >= K) return;
+  const int ncol = min(CPB, K - c0);
+  __shared__ double2 red[NT / 32][CPB];
+  __shared__ double2 wsh[CPB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = m - 2; k >= 0; --k) {
+    const double2 tau = M.tau[k];
+    if (tau.x == 0.0 && tau.y == 0.0) continue;
+    const int n = m - k - 1;
+    const double2* v = M.H + (size_t)k * m + k + 1;
+    double2 acc[CPB];
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) acc[cc] = make_double2(0.0, 0.0);
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 vr = v[r];
+#pragma unroll
+      for (int cc = 0; cc < CPB; ++cc)
+        if (cc < ncol) acc[cc] = cfma_conj(vr, M.U[(size_t)(c0 + cc) * m + k + 1 + r], acc[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < CPB; ++cc) {
+      const double2 t = warp_sum2(acc[cc]);
+      if (lane == 0) red[warp][cc] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < CPB) {
+      double2 t = make_double2(0.0, 0.0);
+      for (int w = 0; w < NT / 32; ++w) t = cadd(t, red[w][threadIdx.x]);
+      wsh[threadIdx.x] = cmul(tau, t);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 vr = v[r];
+#pragma unroll
+      for (int cc = 0; cc < CPB; ++cc) {
+        if (cc < ncol) {
+          double2* u = M.U + (size_t)(c0 + cc) * m + k + 1 + r;
+          *u = csub(*u, cmul(vr, wsh[cc]));
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -810,7 +860,7 @@ int eig_bisect(const EigBatch& b, cudaStream_t s) {
   int km = 0;
   for (int i = 0; i < b.n; ++i) km = std::max(km, std::min(b.a[i].kmax, b.a[i].m));
   if (km == 0) return 0;
-  k_bisect<<<dim3((km + 3) / 4, b.n), 128, 0, s>>>(b);  // four eigenvalues (warps) per block
+  k_bisect<<<dim3((km + 127) / 128, b.n), 128, 0, s>>>(b);  // one eigenvalue per thread
   return 1;
 }
 
@@ -848,6 +898,10 @@ int eig_vectors(const EigBatch& b0, bool mixed, void* const* oz_ws, int* status,
   const int mm = max_m(b);
   k_z_to_u<<<dim3((mm + 31) / 32, (Kmax + 31) / 32, b.n), dim3(32, 8), 0, s>>>(b, in_z2 ? 1 : 0);
   ++launches;
+  if (!mixed) {
+    k_backtransform<<<dim3((Kmax + CPB - 1) / CPB, b.n), NT, 0, s>>>(b);
+    return launches + 1;
+  }
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_bt_T, cudaFuncAttributeMaxDynamicSharedMemorySize, BT * (BT + 1) * 16);

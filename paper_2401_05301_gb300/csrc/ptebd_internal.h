@@ -186,8 +186,9 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
 size_t eig_panel_doubles2(int m);  // complex elements of EigMat::pan for an m x m matrix
 int eig_bisect(const EigBatch& b, cudaStream_t s);
 // Inverse iteration on T for eigenvalues 0..K-1, Newton-Schulz orthonormalisation,
-// and back-transformation U = Q Z in blocks of 64 reflectors (compact WY form; the
-// block products on the exact-digit engine when mixed, FP64 GEMM otherwise).
+// and back-transformation U = Q Z: in the mixed path in blocks of 64 reflectors
+// (compact WY form, block products on the exact-digit engine), in the FP64 path
+// reflector by reflector.
 // Reads a[i].K (set from the eigenvalues).
 int eig_vectors(const EigBatch& b, bool mixed, void* const* oz_ws, int* status, cudaStream_t s);
 
