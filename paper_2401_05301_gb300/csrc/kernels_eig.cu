@@ -813,7 +813,7 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_panel, TD_THREADS, 0);
-    grid = std::max(1, sms * std::min(per_sm, 4));
+    grid = std::max(1, sms * std::min(per_sm, 2));
   }
   int launches = 0;
   for (int k0 = 0; k0 < mm; k0 += TD_NB) {
