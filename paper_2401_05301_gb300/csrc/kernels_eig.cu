@@ -579,6 +579,105 @@ __device__ void finish_w(const EigMat& M, int kp, int jp, double2 alpha) {
   }
 }
 
+
+// Phase 1 of column k in one pass over row k held in registers (m - k <= 256 * P1_R):
+// finish w of column k-1, the alpha part of the pivot row, and the reflector of
+// column k (house_row_block's arithmetic: amax scaling, then the norm).
+constexpr int P1_R = 8;
+__device__ void phase1_regs(const EigMat& M, int k, int j, double* sh, double2* scale_sh) {
+  const int m = M.m, nn = m - k;  // row k from the diagonal: element r <-> column k + r
+  double2* row = M.H + (size_t)k * m;
+  double2* VW = pan_vw(M);
+  double2* WV = pan_wv(M);
+  double2 a[P1_R];
+  double amax = 0.0;
+  if (j > 0) {
+    const double2 alpha = rank2_alpha(M, k - 1, nn);
+    const double2 sft = make_double2(M.p[0].x + 2.0 * alpha.x, M.p[0].y);
+    const double2* vp = M.H + (size_t)(k - 1) * m + k;  // v_{k-1} from index k (vp[0] = 1)
+#pragma unroll
+    for (int u = 0; u < P1_R; ++u) {
+      const int r = threadIdx.x + u * blockDim.x;
+      a[u] = make_double2(0.0, 0.0);
+      if (r < nn) {
+        const double2 v = vp[r];
+        const double2 w = cfma(alpha, v, M.p[r]);  // w_{k-1}(k + r)
+        const size_t rw = (size_t)(k + r) * 2 * TD_NB;
+        VW[rw + TD_NB + j - 1] = w;
+        WV[rw + j - 1] = w;
+        a[u] = csub(row[k + r], cmul(sft, cconj(v)));
+        if (r >= 1) amax = fmax(amax, fmax(fabs(a[u].x), fabs(a[u].y)));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < P1_R; ++u) {
+      const int r = threadIdx.x + u * blockDim.x;
+      a[u] = (r < nn) ? row[k + r] : make_double2(0.0, 0.0);
+      if (r >= 1 && r < nn) amax = fmax(amax, fmax(fabs(a[u].x), fabs(a[u].y)));
+    }
+  }
+  if (nn == 1) {  // last column: no reflector
+    if (threadIdx.x == 0) {
+      M.d[k] = a[0].x;
+      M.e[k] = 0.0;
+      M.tau[k] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    return;
+  }
+  amax = -block_min(-amax, sh);
+  const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
+  double s2 = 0.0;
+#pragma unroll
+  for (int u = 0; u < P1_R; ++u) {
+    const int r = threadIdx.x + u * blockDim.x;
+    if (r >= 2 && r < nn) {
+      const double vx = a[u].x * sinv, vy = a[u].y * sinv;
+      s2 = fma(vx, vx, fma(vy, vy, s2));
+    }
+  }
+  const double xnorm2 = block_sum(s2, sh);
+  if (threadIdx.x == 1 % blockDim.x) {  // the thread holding r = 1 (x[0] of the reflector)
+    const double2 x0 = a[0];
+    const double ar = x0.x * sinv, ai = -x0.y * sinv;
+    double beta;
+    double2 tau, sc;
+    if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
+      beta = x0.x;
+      tau = make_double2(0.0, 0.0);
+      sc = make_double2(0.0, 0.0);
+    } else {
+      const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
+      tau = make_double2((bs - ar) / bs, -ai / bs);
+      const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
+      sc = make_double2(zr / den * sinv, -zi / den * sinv);
+      beta = bs * amax;
+    }
+    M.e[k] = beta;
+    M.tau[k] = tau;
+    *scale_sh = sc;
+  }
+  if (threadIdx.x == 0) M.d[k] = a[0].x;
+  __syncthreads();
+  const double2 sc = *scale_sh;
+#pragma unroll
+  for (int u = 0; u < P1_R; ++u) {
+    const int r = threadIdx.x + u * blockDim.x;
+    if (r < nn) {
+      double2 out = a[u];  // r = 0: the diagonal element
+      if (r >= 1) {
+        out = (r == 1) ? make_double2(1.0, 0.0) : cmul(cconj(a[u]), sc);
+        const size_t rw = (size_t)(k + r) * 2 * TD_NB;
+        VW[rw + j] = out;
+        WV[rw + TD_NB + j] = out;
+      }
+      row[k + r] = out;
+    }
+  }
+  __syncthreads();
+}
+
 // Blocked Householder tridiagonalisation, one panel of columns [k0, k1) per
 // cooperative launch (the trailing matrix from k0 on is current when it starts).
 // Column k (panel index j) is reduced against A(k) = A(k0) - sum_{i<j} (v_i w_i^+ +
@@ -604,11 +703,15 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
   unsigned int target = 0;  // barrier count expected at the next grid_sync
   for (int k = k0; k < k1; ++k) {
     const int j = k - k0;
-    // ---- phase 1
+    // ---- phase 1 (row k in registers when it fits, else in memory passes)
     for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
       const EigMat& M = b.a[mi];
       const int m = M.m;
       if (k >= m) continue;
+      if (m - k <= P1_R * (int)blockDim.x) {
+        phase1_regs(M, k, j, red_sh, &scale_sh);
+        continue;
+      }
       double2* row = M.H + (size_t)k * m;
       if (j > 0) {
         // Row k was brought to A(k) in phase 3 of column k-1 except for the alpha
