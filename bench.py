@@ -34,7 +34,8 @@ if ROOT not in sys.path:
 import workloads  # noqa: E402
 
 WL = workloads.TRUNC_L32
-WORKLOADS = {"trunc_L32": workloads.TRUNC_L32, "parity_L8": workloads.PARITY_L8}
+WORKLOADS = {"trunc_L32": workloads.TRUNC_L32, "parity_L8": workloads.PARITY_L8,
+             "sample_L16_d5_chi1024": workloads.SAMPLE_L16_D5}
 
 
 def gates_per_step(L: int) -> int:
@@ -169,6 +170,51 @@ def served_measurement(stream_ptr):
             "peak_active": srv.peak_active}
 
 
+def batched_measurement(stream_ptr, steps: int = 10):
+    """The 48 seeded simulations of the batched configuration (L in 16..64, chi_max in 64..512, d = 4),
+    from their CDW product states: `tebd_batch_step` over all of them (one workspace slot each, so a
+    layer's triples of many simulations share every grouped launch) against stepping each alone with
+    its own default workspace.  Both start after one untimed step; mixed path."""
+    import torch
+    from paper_2401_05301_gb300 import TEBD, batch_step
+    wls = workloads.batch48()
+
+    def make(w, slots):
+        g = TEBD(w.L, w.n_max, w.chi_max, w.U, w.J, w.Jnnn, w.K, w.jc, w.dt, precision=1, stream=stream_ptr)
+        if slots:
+            g.set_option("max_slots", slots)
+        g.init_product(workloads.cdw(w.L))
+        return g
+
+    sims = [make(w, 1) for w in wls]
+    batch_step(sims, 1)
+    torch.cuda.synchronize()
+    g0 = sum(g.counters()[0] for g in sims)
+    t = time.perf_counter()
+    batch_step(sims, steps)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    gb = sum(g.counters()[0] for g in sims) - g0
+    for g in sims:
+        g.close()
+    ta, ga = 0.0, 0
+    for w in wls:
+        g = make(w, 0)
+        g.step(1)
+        torch.cuda.synchronize()
+        c0 = g.counters()[0]
+        t = time.perf_counter()
+        g.step(steps)
+        torch.cuda.synchronize()
+        ta += time.perf_counter() - t
+        ga += g.counters()[0] - c0
+        g.close()
+    return {"workload": f"48 seeded simulations (L 16..64, chi_max 64..512, d=4) from CDW product states, "
+                        f"{steps} steps after one untimed step", "unit": UNIT,
+            "batched_value": gb / tb, "batched_s": tb, "alone_value": ga / ta, "alone_s": ta,
+            "gate_updates": gb}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -202,6 +248,7 @@ def main():
                     help="mixed: 3xTF32 tensor-core contractions + FP64 SVD (headline); the FP64 path is timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 48-simulation batched measurement")
     ap.add_argument("--workload", default="trunc_L32", choices=sorted(WORKLOADS),
                     help="trunc_L32 is the measured configuration; parity_L8 is a small case for profiling")
     args = ap.parse_args()
@@ -342,6 +389,9 @@ def main():
     served = None
     if not args.no_served and ws == 1:
         served = served_measurement(stream.cuda_stream)
+    batched = None
+    if not args.no_batched and ws == 1 and args.workload == "trunc_L32":
+        batched = batched_measurement(stream.cuda_stream)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -359,7 +409,8 @@ def main():
             "data": "synthetic", "config": config(args.precision),
             "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
-            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "served": served}
+            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "served": served,
+            "batched": batched}
     print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:

@@ -74,6 +74,10 @@ TRUNC_L32 = Workload("trunc_L32_d4_chi256", L=32, n_max=3, chi_max=256, U=5.0, J
                      jc=16.5, dt=0.01, t_end=6.0, w_cut=1e-10)
 MIXED_L64 = Workload("mixed_L64_d5_chi1024", L=64, n_max=4, chi_max=1024, U=3.0, J=1.0, Jnnn=0.1, K=0.003,
                      jc=32.5, dt=0.005, t_end=8.0, w_cut=0.0)
+# The same physics on a 16-site chain: bonds 5..11 saturate at chi_max = 1024 (5^5 > 1024), so one
+# step holds the chi_max = 1024, d = 5 local updates in about a minute of GPU time.
+SAMPLE_L16_D5 = Workload("sample_L16_d5_chi1024", L=16, n_max=4, chi_max=1024, U=3.0, J=1.0, Jnnn=0.1, K=0.003,
+                         jc=8.5, dt=0.005, t_end=8.0, w_cut=0.0)
 
 
 def batch48(seed: int = SEED):
