@@ -305,23 +305,22 @@ def main():
         t_max = float(t.item())
     value = gates_per_step(WL.L) * args.steps * ws / (t_max / 1e3)
 
-    # -- the plain FP64 path on the same state, for "mixed vs FP64" ------------------
-    fp64 = None
-    if prec == 1:
-        g64 = TEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
-                   eps_rel=WL.eps_rel, precision=0, stream=stream.cuda_stream)
-        g64.set_state(B, lam)
+    # -- the plain FP64 path and the FP64-accurate tensor-core path on the same state ----
+    def time_path(precision):
+        gp = TEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
+                  eps_rel=WL.eps_rel, precision=precision, stream=stream.cuda_stream)
+        gp.set_state(B, lam)
         for _ in range(args.warmup):
-            g64.step(1)
-            g64.measure()
-        g64.set_option("profile", 1)
+            gp.step(1)
+            gp.measure()
+        gp.set_option("profile", 1)
         barrier()
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            g64.step(1)
-            g64.measure()
+            gp.step(1)
+            gp.measure()
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
@@ -329,10 +328,17 @@ def main():
             t = torch.tensor([fms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             fms = float(t.item())
-        p64 = g64.profile()
-        fp64 = {"value": gates_per_step(WL.L) * args.steps * ws / (fms / 1e3), "unit": UNIT,
-                "ms_per_step": fms / args.steps, "classes_ms": {k: round(v[0], 3) for k, v in p64.items()}}
-        g64.close()
+        pp = gp.profile()
+        gp.close()
+        return {"value": gates_per_step(WL.L) * args.steps * ws / (fms / 1e3), "unit": UNIT,
+                "ms_per_step": fms / args.steps, "classes_ms": {k: round(v[0], 3) for k, v in pp.items()}}
+
+    fp64 = exact = None
+    if prec == 1:
+        fp64 = time_path(0)
+        exact = time_path(2)
+        exact["note"] = ("precision 2: every large product on the exact-digit tensor-core engine "
+                         "(FP64-accurate; parity with the oracle at the FP64 bound)")
 
     # -- end to end through the C ABI with host buffers ---------------------------
     pinned_B = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory().numpy() for b in B]
@@ -409,8 +415,8 @@ def main():
             "data": "synthetic", "config": config(args.precision),
             "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
-            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "served": served,
-            "batched": batched}
+            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "exact_path": exact,
+            "served": served, "batched": batched}
     print(json.dumps(line), flush=True)
     g.close()
     if ws > 1:

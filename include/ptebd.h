@@ -58,8 +58,12 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
  *   "w_cut"   discarded-weight cut: keep the fewest values whose discarded
  *             weight sum_{i>chi'} p_i <= w_cut, p_i = s_i^2 / sum s^2  (default 0)
  *   "eps_rel" drop every value with p_i <= eps_rel (default 1e-12, the paper's eps)
- *   "precision" 0 = FP64 everywhere (default); 1 = mixed: theta/gate/rebuild
- *             contractions as 3xTF32 on tensor cores, SVD stage in FP64
+ *   "precision" 0 = FP64 on the CUDA cores everywhere (default);
+ *             1 = mixed: theta/gate/rebuild contractions as split 3xTF32 on the
+ *             tensor cores (FP32 accumulation), the SVD stage FP64-accurate (its
+ *             dense products as exact-digit bf16 tensor-core products);
+ *             2 = FP64-accurate throughout: the contractions too as exact-digit
+ *             tensor-core products (the small gate product on FP64 CUDA cores)
  *   "max_slots" cap on triples processed concurrently (0 = automatic)
  * Unknown key or out-of-range value: TEBD_ERR_ARG. */
 int tebd_set_option(tebd_handle h, const char* key, double value);
@@ -83,9 +87,9 @@ int tebd_step(tebd_handle h, int n_steps);
 /* Device bytes a handle with these sizes holds once stepped and measured
  * (state, gates, workspace for min(triples per layer, 24, max_slots > 0 ?
  * max_slots : 24) concurrent local updates, measurement buffers; precision 1
- * adds the digit planes of the mixed path's Gram and projection products),
+ * and 2 add the digit planes of the exact-digit products),
  * written to *bytes.  Host-only arithmetic: used to admit simulations by an
- * HBM budget before creating them.  precision must be 0 or 1. */
+ * HBM budget before creating them.  precision must be 0, 1 or 2. */
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
 /* Batched form: advance n distinct handles (simulations with any L, n_max,

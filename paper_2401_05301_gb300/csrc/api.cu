@@ -207,7 +207,12 @@ double oz_slot_bytes(long long capmax, long long d, long long chi_max) {
   const long long mm = capmax * d, n1max = d * d * capmax, kc = std::min<long long>(mm, chi_max);
   return (double)std::max({oz_workspace_bytes((int)mm, (int)mm, (int)n1max, true),
                            oz_workspace_bytes((int)kc, (int)n1max, (int)mm, false),
-                           oz_workspace_bytes((int)kc, (int)mm, (int)mm, false)});
+                           oz_workspace_bytes((int)kc, (int)mm, (int)mm, false),
+                           // contractions of precision 2: B_i B_{i+1}, X B_{i+2}, C V1^+, V1^+ V2^+
+                           oz_workspace_bytes((int)mm, (int)(d * capmax), (int)capmax, false),
+                           oz_workspace_bytes((int)(mm * d), (int)(d * capmax), (int)capmax, false),
+                           oz_workspace_bytes((int)mm, (int)kc, (int)n1max, false),
+                           oz_workspace_bytes((int)mm, (int)kc, (int)mm, false)});
 }
 
 double slot_bytes_for(long long capmax, long long d, long long chi_max, int precision) {
@@ -216,7 +221,7 @@ double slot_bytes_for(long long capmax, long long d, long long chi_max, int prec
   return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 3.0 * mm +
                  EIG_PARTS + kc * mm) +
          8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1) + 16.0 * eig_panel_doubles2((int)mm) +
-         (precision == 1 ? oz_slot_bytes(capmax, d, chi_max) : 0.0);
+         (precision >= 1 ? oz_slot_bytes(capmax, d, chi_max) : 0.0);
 }
 
 std::vector<int> bond_caps(int L, int d, int chi_max) {
@@ -266,8 +271,8 @@ int alloc_workspace(tebd_ctx* c) {
     S.perm = dalloc<int>(c, mm);
     S.chi = dalloc<int>(c, 1);
     S.pan = dalloc<double2>(c, eig_panel_doubles2((int)mm));
-    if (c->precision == 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max));
-    if ((c->precision == 1 && !S.oz) || !S.pan || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
+    if (c->precision >= 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max));
+    if ((c->precision >= 1 && !S.oz) || !S.pan || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
         !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
       if (s == 0) return TEBD_ERR_OOM;
       break;
@@ -344,7 +349,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     for (int t = 0; t < eb.n; ++t) w += 16.0 / 3.0 * std::pow((double)eb.a[t].m, 3);
     ProfScope ps(c, TEBD_PROF_TRIDIAG, w);
     c->launches += eig_trace(eb, c->stream);
-    const int nl = eig_tridiagonalize(eb, c->precision == 1, oz_ws, c->d_status, c->stream);
+    const int nl = eig_tridiagonalize(eb, c->precision >= 1, oz_ws, c->d_status, c->stream);
     if (nl < 0) {
       cudaGetLastError();
       std::fprintf(stderr, "ptebd: cooperative launch of the tridiagonal reduction refused\n");
@@ -405,7 +410,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
       w += 8.0 * m * m * K + 12.0 * m * K * K;
     }
     ProfScope ps(c, TEBD_PROF_EIGVEC, w);
-    c->launches += eig_vectors(eb, c->precision == 1, oz_ws, c->d_status, c->stream);
+    c->launches += eig_vectors(eb, c->precision >= 1, oz_ws, c->d_status, c->stream);
   }
   for (size_t t = 0; t < ts.size(); ++t) {
     const EigMat& M = eb.a[t];
@@ -474,6 +479,24 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   return TEBD_OK;
 }
 
+// C = alpha A op(B) on the exact-digit engine: A is M x K (row stride lda); b(j, k) =
+// B[j * b_rs + k * b_ks], conjugated if b_conj (so op(B) = B with (1, ldb), B^+ with (ldb, 1, conj)).
+OzProb oz_plain(const double2* A, long long lda, const double2* B, long long b_rs, long long b_ks, int b_conj, int M,
+                int N, int K, double2* C, long long ldc, double alpha, void* ws) {
+  OzProb q{};
+  q.a = OzOperand{A, lda, 1, nullptr, 1, 0};
+  q.b = OzOperand{B, b_rs, b_ks, nullptr, 1, b_conj};
+  q.M = M;
+  q.N = N;
+  q.K = K;
+  q.C = C;
+  q.ldc = ldc;
+  q.alpha = alpha;
+  q.row_div = q.col_div = 1;
+  q.ws = ws;
+  return q;
+}
+
 // Mixed path, exact-digit tensor-core products (FP64 accuracy):
 // Gram H = (lam X)(lam X)^+ of X (m x n, row-major), rows scaled by lam[r / d].
 OzProb oz_gram(const double2* X, int m, int n, const double* lam, int d, double2* H, void* ws) {
@@ -516,7 +539,7 @@ OzProb oz_project(const double2* U, int K, int m, const double* lam, int d, cons
 // buffer (rows x rows) and Th (rows x n).  second: V2 = B_{i+2}, else V1^+.
 int reorthonormalise(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   cudaStream_t s = c->stream;
-  const bool mixed = c->precision == 1;
+  const bool mixed = c->precision >= 1;  // exact-digit products (precision 1 and 2)
   Gemm gG(true, OP_N, OP_C), gA(true, OP_N, OP_N);
   std::vector<OzProb> oG, oA;
   std::vector<PolarArgs> pa;
@@ -566,7 +589,9 @@ int reorthonormalise(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
 // contraction path for the whole batch.
 int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   cudaStream_t s = c->stream;
-  const bool mixed = c->precision == 1;
+  // precision 1: contractions as split 3xTF32; 2: contractions as exact-digit products.
+  // Both: the SVD's dense products on the exact-digit engine (FP64-accurate).
+  const bool tf32 = c->precision == 1, exact = c->precision == 2, mixed = c->precision >= 1;
   if (mixed)
     for (auto& T : ts)
       if (int r = ensure_oz(T.h)) return r;
@@ -605,9 +630,25 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g1.launch(s, mixed, c->d_status);
-      c->launches += g2.launch(s, mixed, c->d_status);
-      c->launches += g3.launch(s, mixed, c->d_status);
+      if (exact) {  // X = B_i B_{i+1}, then Th = X B_{i+2}; the gate stays on the FP64 GEMM
+        std::vector<OzProb> o1, o2;
+        for (auto& T : ts) {
+          tebd_ctx* o = T.h;
+          const int d = o->d;
+          const Slot& S = o->slots[T.slot];
+          o1.push_back(oz_plain(o->B[T.i], T.c1, o->B[T.i + 1], 1, (long long)d * T.c2, 0, T.chl * d, d * T.c2, T.c1,
+                                S.X, (long long)d * T.c2, 1.0, S.oz));
+          o2.push_back(oz_plain(S.X, T.c2, o->B[T.i + 2], 1, (long long)d * T.chr, 0, T.chl * d * d, d * T.chr, T.c2,
+                                S.Th, (long long)d * T.chr, 1.0, S.oz));
+        }
+        c->launches += oz_gemm_launch(o1, c->d_status, s);
+        c->launches += oz_gemm_launch(o2, c->d_status, s);
+        c->launches += g3.launch(s);
+      } else {
+        c->launches += g1.launch(s, tf32, c->d_status);
+        c->launches += g2.launch(s, tf32, c->d_status);
+        c->launches += g3.launch(s, tf32, c->d_status);
+      }
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -676,7 +717,17 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-      c->launches += g6.launch(s, mixed, c->d_status);
+      if (exact) {  // B_i = C V1^+ / ||s||
+        std::vector<OzProb> o6;
+        for (auto& T : ts) {
+          const Slot& S = T.h->slots[T.slot];
+          o6.push_back(oz_plain(S.Cb, T.n1, S.V1h, T.n1, 1, 1, T.m1, T.chi1, T.n1, T.h->B[T.i], T.chi1,
+                                1.0 / T.norm1, S.oz));
+        }
+        c->launches += oz_gemm_launch(o6, c->d_status, s);
+      } else {
+        c->launches += g6.launch(s, tf32, c->d_status);
+      }
     }
     {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -724,7 +775,17 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     for (auto& T : ts) w += 8.0 * (double)T.m2 * T.chi2 * T.n2;
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, w);
-      c->launches += g9.launch(s, mixed, c->d_status);
+      if (exact) {  // B_{i+1} = V1^+ V2 / ||s2||
+        std::vector<OzProb> o9;
+        for (auto& T : ts) {
+          const Slot& S = T.h->slots[T.slot];
+          o9.push_back(oz_plain(S.V1h, T.n2, T.h->B[T.i + 2], T.n2, 1, 1, T.m2, T.chi2, T.n2, T.h->B[T.i + 1],
+                                T.chi2, 1.0 / T.norm2, S.oz));
+        }
+        c->launches += oz_gemm_launch(o9, c->d_status, s);
+      } else {
+        c->launches += g9.launch(s, tf32, c->d_status);
+      }
     }
     if (int r = check_launch(c)) return r;
   }
@@ -947,7 +1008,7 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
     if (value < 0 || value >= 1) return TEBD_ERR_ARG;
     h->eps_rel = value;
   } else if (k == "precision") {
-    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if (value != 0.0 && value != 1.0 && value != 2.0) return TEBD_ERR_ARG;
     h->precision = (int)value;
   } else if (k == "profile") {
     if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
@@ -1039,7 +1100,7 @@ int tebd_step(tebd_handle h, int n_steps) {
 
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes) {
   if (!bytes || L < 3 || n_max < 1 || n_max > 7 || chi_max < 1 || max_slots < 0) return TEBD_ERR_ARG;
-  if (precision != 0 && precision != 1) return TEBD_ERR_ARG;
+  if (precision < 0 || precision > 2) return TEBD_ERR_ARG;
   const int d = n_max + 1, D = d * d * d;
   const std::vector<int> cap = bond_caps(L, d, chi_max);
   double b = 0.0;

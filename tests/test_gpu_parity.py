@@ -15,12 +15,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-9
 
 
-def _pair(lib, wl, **kw):
+def _pair(lib, wl, precision=None, **kw):
     from paper_2401_05301_gb300 import TEBD
     args = dict(L=wl.L, n_max=wl.n_max, chi_max=wl.chi_max, U=wl.U, J=wl.J, Jnnn=wl.Jnnn, K=wl.K, jc=wl.jc,
                 dt=wl.dt, w_cut=wl.w_cut, eps_rel=wl.eps_rel)
     args.update(kw)
-    g = TEBD(**args)
+    g = TEBD(**args, precision=precision)
     o = OracleTEBD(**args)
     return g, o
 
@@ -65,6 +65,15 @@ def test_parity_L32_truncating(lib):
     wl = workloads.TRUNC_L32
     worst = _compare_run(lib, wl, 100, 10)
     print(f"L32 parity: max |delta| = {worst:.3e}")
+
+
+@pytest.mark.parametrize("name,steps,every", [("PARITY_L8", 400, 10), ("TRUNC_L32", 100, 10)])
+def test_exact_digit_precision_holds_fp64_bound(lib, name, steps, every):
+    """precision 2: every large product (contractions, Gram, projection, reduction
+    updates, back-transformation) on the exact-digit tensor-core engine; the FP64
+    parity bound must still hold."""
+    worst = _compare_run(lib, getattr(workloads, name), steps, every, precision=2)
+    print(f"{name} exact-digit parity: max |delta| = {worst:.3e}")
 
 
 def test_hard_core_free_fermions_on_gpu(lib):
