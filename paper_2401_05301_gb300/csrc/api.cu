@@ -803,31 +803,34 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
 // simulation uses at most its own number of workspace slots.  c drives.
 int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, int tidx) {
   struct Pending { tebd_ctx* h; int i; };
-  std::vector<Pending> all;
+  std::vector<Pending> rest;
   for (tebd_ctx* h : hs)
-    for (int i = residue; i + 2 < h->L; i += 3) all.push_back({h, i});
-  size_t next = 0;
-  while (next < all.size()) {
+    for (int i = residue; i + 2 < h->L; i += 3) rest.push_back({h, i});
+  // Each chunk takes, in order, every pending triple whose simulation still has a free
+  // workspace slot in this chunk, up to EIG_MAXP triples; the triples of a layer are
+  // disjoint, so any grouping gives the same (bitwise) result.
+  while (!rest.empty()) {
     std::vector<Triple> ts;
     std::vector<std::pair<tebd_ctx*, int>> used;  // slots taken per simulation in this chunk
-    while (next < all.size() && (int)ts.size() < EIG_MAXP) {
-      tebd_ctx* h = all[next].h;
-      int k = 0;
+    std::vector<Pending> later;
+    for (const Pending& p : rest) {
+      int* k = nullptr;
       for (auto& u : used)
-        if (u.first == h) k = u.second;
-      if (k >= (int)h->slots.size()) break;  // this simulation's slots are full: close the chunk
+        if (u.first == p.h) k = &u.second;
+      const int taken = k ? *k : 0;
+      if ((int)ts.size() >= EIG_MAXP || taken >= (int)p.h->slots.size()) {
+        later.push_back(p);
+        continue;
+      }
       Triple T{};
-      T.h = h;
-      T.i = all[next].i;
-      T.slot = k;
+      T.h = p.h;
+      T.i = p.i;
+      T.slot = taken;
       ts.push_back(T);
-      bool found = false;
-      for (auto& u : used)
-        if (u.first == h) { ++u.second; found = true; }
-      if (!found) used.push_back({h, 1});
-      ++next;
+      if (k) ++*k; else used.push_back({p.h, 1});
     }
     if (int r = update_chunk(c, ts, tidx)) return r;
+    rest.swap(later);
   }
   return TEBD_OK;
 }
