@@ -407,8 +407,10 @@ def main():
                "sample": f"{n_cpu} three-site updates of the saturated chi=256 state ({secs:.1f} s)"}
 
     line = {"metric": METRIC,
-            "metric_detail": ("value: mixed path (3xTF32 tensor-core contractions, FP64 SVD); fp64_path: the plain "
-                              "FP64 GPU method on the same state" if prec == 1 else "value: plain FP64 GPU method"),
+            "metric_detail": ("value: mixed path (3xTF32 tensor-core contractions; SVD stage FP64-accurate, its "
+                              "products as exact-digit tensor-core products); fp64_path: the plain FP64 GPU method on "
+                              "the same state; exact_path: FP64-accurate throughout on the tensor cores"
+                              if prec == 1 else "value: plain FP64 GPU method"),
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+tf32x3",
