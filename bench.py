@@ -122,6 +122,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (the job's time is its slowest replica's)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(updates_per_rank: int, ws: int, seconds_max: float) -> float:
+    """Whole-job throughput of ws replicas that each did updates_per_rank gate updates."""
+    return updates_per_rank * ws / seconds_max
+
+
 def oracle_sample(n_gates: int, seed_state):
     """Time the oracle on n_gates three-site updates of the saturated state (layer A order)."""
     from oracle.tebd import TEBD as OracleTEBD
@@ -298,12 +314,8 @@ def main():
     _, l1 = g.counters()
     prof = g.profile()
     g.set_option("profile", 0)
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = gates_per_step(WL.L) * args.steps * ws / (t_max / 1e3)
+    t_max = max_over_ranks(ms, ws)
+    value = job_value(gates_per_step(WL.L) * args.steps, ws, t_max / 1e3)
 
     # -- the plain FP64 path and the FP64-accurate tensor-core path on the same state ----
     def time_path(precision):
@@ -323,14 +335,10 @@ def main():
             gp.measure()
         f1.record(stream)
         torch.cuda.synchronize()
-        fms = f0.elapsed_time(f1)
-        if ws > 1:
-            t = torch.tensor([fms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            fms = float(t.item())
+        fms = max_over_ranks(f0.elapsed_time(f1), ws)
         pp = gp.profile()
         gp.close()
-        return {"value": gates_per_step(WL.L) * args.steps * ws / (fms / 1e3), "unit": UNIT,
+        return {"value": job_value(gates_per_step(WL.L) * args.steps, ws, fms / 1e3), "unit": UNIT,
                 "ms_per_step": fms / args.steps, "classes_ms": {k: round(v[0], 3) for k, v in pp.items()}}
 
     fp64 = exact = None
@@ -354,12 +362,8 @@ def main():
         g.step(1)
         g.measure()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = gates_per_step(WL.L) * e2e_steps * ws / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = job_value(gates_per_step(WL.L) * e2e_steps, ws, e2e_s)
 
     if rank != 0:
         if ws > 1:
