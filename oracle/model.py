@@ -107,16 +107,30 @@ def layer_of(j: int) -> str:
     return {1: "A", 2: "B", 0: "C"}[j % 3]
 
 
-def step_schedule(L: int, dt: float):
-    """One symmetric second-order step: A(dt/2) B(dt/2) C(dt) B(dt/2) A(dt/2).
+def step_schedule(L: int, dt: float, order: int = 2):
+    """One step of the layer schedule: a list of (list_of_triples_1based, tau).
 
-    Returns a list of (list_of_triples_1based, tau).  Strang splitting of the
-    three layer Hamiltonians (second-order Trotter, Sec. II B / Appendix A).
-    Reading M: the trailing A(dt/2) is never merged with the next step's.
+    order 2: the symmetric step A(dt/2) B(dt/2) C(dt) B(dt/2) A(dt/2) (Strang
+    splitting of the three layer Hamiltonians; second-order Trotter, Sec. II B /
+    Appendix A).  order 4: Suzuki's fourth-order fractal composition of that step,
+    S2(p dt) S2(p dt) S2((1-4p) dt) S2(p dt) S2(p dt) with p = 1/(4 - 4^(1/3)); the
+    paper cross-checks its second-order results against a fourth-order split
+    (Appendix A), without fixing the composition.  Reading M: adjacent half-step
+    layers (inside a step or across steps) are never merged.
     """
     trip = {lab: [j for j in range(1, L - 1) if layer_of(j) == lab] for lab in "ABC"}
-    return [(trip["A"], dt / 2), (trip["B"], dt / 2), (trip["C"], dt),
-            (trip["B"], dt / 2), (trip["A"], dt / 2)]
+
+    def s2(tau):
+        return [(trip["A"], tau / 2), (trip["B"], tau / 2), (trip["C"], tau),
+                (trip["B"], tau / 2), (trip["A"], tau / 2)]
+
+    if order == 2:
+        return s2(dt)
+    if order == 4:
+        p = 1.0 / (4.0 - 4.0 ** (1.0 / 3.0))
+        q = 1.0 - 4.0 * p
+        return s2(p * dt) + s2(p * dt) + s2(q * dt) + s2(p * dt) + s2(p * dt)
+    raise ValueError("order must be 2 or 4")
 
 
 def cdw_occupation(L: int) -> np.ndarray:

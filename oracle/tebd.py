@@ -72,13 +72,14 @@ class TEBD:
     units of Sec. I A); w_cut and eps_rel are reading T's tolerances.
     """
 
-    def __init__(self, L, n_max, chi_max, U, J, Jnnn, K, jc, dt, w_cut=0.0, eps_rel=1e-12):
+    def __init__(self, L, n_max, chi_max, U, J, Jnnn, K, jc, dt, w_cut=0.0, eps_rel=1e-12, order=2):
         if L < 3:
             raise ValueError("L >= 3 required (three-site gates)")
         self.L, self.n_max, self.d = L, n_max, n_max + 1
         self.chi_max, self.dt = chi_max, dt
         self.U, self.J, self.Jnnn, self.K, self.jc = U, J, Jnnn, K, jc
         self.w_cut, self.eps_rel = w_cut, eps_rel
+        self.order = order
         self.h = [model.three_site_term(j, L, n_max, U, J, Jnnn, K, jc) for j in range(1, L - 1)]
         self._gates = {}
         self.B = None
@@ -153,8 +154,8 @@ class TEBD:
             self.apply_gate(j - 1, self.gate(j, tau))
 
     def step(self, n: int = 1):
-        """n full second-order steps (model.step_schedule)."""
-        sched = model.step_schedule(self.L, self.dt)
+        """n full steps of the Trotter split of the given order (model.step_schedule)."""
+        sched = model.step_schedule(self.L, self.dt, self.order)
         for _ in range(n):
             for triples, tau in sched:
                 self.layer(triples, tau)

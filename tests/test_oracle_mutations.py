@@ -109,3 +109,29 @@ def test_catches_first_order_schedule():
     finally:
         model.step_schedule = orig
     assert not (3.5 <= errs[0] / errs[1] <= 4.5)
+
+
+
+def test_catches_wrong_fourth_order_weights():
+    """Middle weight 1 - 2p instead of 1 - 4p: the 4th-order step no longer spans dt,
+    and the exact-ED comparison of the convergence pin fails by orders of magnitude."""
+    good = model.step_schedule
+
+    def bad(L, dt, order=2):
+        if order != 4:
+            return good(L, dt, order)
+        p = 1.0 / (4.0 - 4.0 ** (1.0 / 3.0))
+        return good(L, p * dt) * 2 + good(L, (1.0 - 2.0 * p) * dt) + good(L, p * dt) * 2
+
+    wl = workloads.PARITY_L8
+    occ = wl.occupation()
+    ex = ed.SectorED(wl.L, wl.n_max, occ, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc)
+    n_ex, _ = ex.observables(1.0)
+    T = TEBD(wl.L, wl.n_max, wl.chi_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, 0.05, eps_rel=1e-24, order=4)
+    try:
+        model.step_schedule = bad
+        T.init_product(occ)
+        T.step(20)
+    finally:
+        model.step_schedule = good
+    assert np.max(np.abs(T.densities() - n_ex)) > 1e-3  # the correct split is within 2.3e-7 here

@@ -255,3 +255,48 @@ def test_local_error_tracks_scaled_discarded_weight():
     err = np.max(np.abs(ref.densities() - cut.densities()))
     assert cut.w_total > 0
     assert err < 50 * cut.w_total
+
+
+# -- fourth-order split (Appendix A cross-check; Suzuki's composition) ---------------
+
+def _fourth_order_error(dt, schedule=model.step_schedule):
+    """Max deviation of 4th-order TEBD from exact fixed-N ED at t = 1 (no truncation)."""
+    wl = workloads.PARITY_L8
+    occ = wl.occupation()
+    ex = ed.SectorED(wl.L, wl.n_max, occ, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc)
+    n_ex, C_ex = ex.observables(1.0)
+    T = _tebd(wl, dt=dt, eps_rel=1e-24)
+    T.order = 4
+    orig = model.step_schedule
+    try:
+        model.step_schedule = schedule
+        T.init_product(occ)
+        T.step(int(round(1.0 / dt)))
+    finally:
+        model.step_schedule = orig
+    return max(np.max(np.abs(T.densities() - n_ex)), np.max(np.abs(T.correlators() - C_ex)))
+
+
+def test_trotter_error_is_fourth_order():
+    """Exact sector ED vs 4th-order TEBD at dt = 0.1 and 0.05: error ratio in [14, 19] (2^4 = 16)."""
+    errs = [_fourth_order_error(dt) for dt in (0.1, 0.05)]
+    ratio = errs[0] / errs[1]
+    assert 14.0 <= ratio <= 19.0, (errs, ratio)
+    assert errs[1] < 1e-6
+
+
+def test_fourth_order_tebd_matches_dense_trotter():
+    """The 25-layer 4th-order step on the MPS equals the same gate sequence on the dense vector."""
+    L, n_max, dt = 6, 2, 0.07
+    T = TEBD(L, n_max, 10 ** 6, 3.0, 1.0, 0.2, 0.05, 3.2, dt, w_cut=0.0, eps_rel=1e-24, order=4)
+    occ = workloads.cdw(L)
+    T.init_product(occ)
+    psi = ed.dense_product(occ, n_max + 1)
+    sched = model.step_schedule(L, dt, 4)
+    assert len(sched) == 25 and abs(sum(tau for trip, tau in sched if trip == sched[2][0]) - dt) < 1e-15
+    for _ in range(5):
+        T.step()
+        psi = ed.dense_trotter_step(psi, T.gate, sched, n_max + 1)
+    n_d, C_d = ed.dense_observables(psi)
+    assert np.max(np.abs(T.densities() - n_d)) < 1e-12
+    assert np.max(np.abs(T.correlators() - C_d)) < 1e-12
