@@ -65,6 +65,11 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
  *             2 = FP64-accurate throughout: the contractions too as exact-digit
  *             tensor-core products (the small gate product on FP64 CUDA cores)
  *   "max_slots" cap on triples processed concurrently (0 = automatic)
+ *   "trotter_order" 2 (default): the symmetric step A(dt/2) B(dt/2) C(dt) B(dt/2)
+ *             A(dt/2); 4: Suzuki's fourth-order composition of that step,
+ *             S2(p dt)^2 S2((1-4p) dt) S2(p dt)^2 with p = 1/(4 - 4^(1/3)) (25 layers;
+ *             the cross-check of Appendix A).  Changing it rebuilds the gate table
+ *             (four time arguments instead of two) and synchronises the stream.
  * Unknown key or out-of-range value: TEBD_ERR_ARG. */
 int tebd_set_option(tebd_handle h, const char* key, double value);
 
@@ -89,7 +94,8 @@ int tebd_step(tebd_handle h, int n_steps);
  * max_slots : 24) concurrent local updates, measurement buffers; precision 1
  * and 2 add the digit planes of the exact-digit products),
  * written to *bytes.  Host-only arithmetic: used to admit simulations by an
- * HBM budget before creating them.  precision must be 0, 1 or 2. */
+ * HBM budget before creating them.  precision must be 0, 1 or 2.  The gate
+ * table is counted for trotter_order 2 (order 4 holds twice as many gates). */
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
 /* Batched form: advance n distinct handles (simulations with any L, n_max,

@@ -47,6 +47,7 @@ struct tebd_ctx {
   double U = 0, J = 0, Jnnn = 0, K = 0, jc = 0, dt = 0;
   double w_cut = 0.0, eps_rel = 1e-12;
   int precision = 0, max_slots = 0;
+  int order = 2;  // Trotter order: 2 or 4 (gate table and layer schedule follow it)
   cudaStream_t stream = nullptr;
   int device = 0;
   int sticky = TEBD_OK;
@@ -228,6 +229,57 @@ std::vector<int> bond_caps(int L, int d, int chi_max) {
   std::vector<int> cap(L + 1);
   for (int k = 0; k <= L; ++k) cap[k] = (int)ipow_cap(d, std::min(k, L - k), chi_max);
   return cap;
+}
+
+// Time arguments of the gate table: order 2 uses {dt/2, dt}; order 4 (Suzuki's
+// composition S2(p dt)^2 S2((1-4p) dt) S2(p dt)^2, p = 1/(4 - 4^(1/3))) uses
+// {p dt/2, p dt, (1-4p) dt/2, (1-4p) dt}.
+std::vector<double> gate_taus(const tebd_ctx* c) {
+  if (c->order == 2) return {0.5 * c->dt, c->dt};
+  const double p = 1.0 / (4.0 - std::cbrt(4.0)), q = 1.0 - 4.0 * p;
+  return {0.5 * p * c->dt, p * c->dt, 0.5 * q * c->dt, q * c->dt};
+}
+
+// Layers of one step as (residue, index into the gate table): the symmetric
+// second-order step A(t/2) B(t/2) C(t) B(t/2) A(t/2), once (order 2) or composed
+// five times (order 4).  Adjacent half-step layers are never merged.
+std::vector<std::pair<int, int>> step_layers(const tebd_ctx* c) {
+  std::vector<std::pair<int, int>> out;
+  auto s2 = [&](int half, int full) {
+    const std::pair<int, int> l[5] = {{0, half}, {1, half}, {2, full}, {1, half}, {0, half}};
+    out.insert(out.end(), l, l + 5);
+  };
+  if (c->order == 2) {
+    s2(0, 1);
+  } else {
+    s2(0, 1); s2(0, 1); s2(2, 3); s2(0, 1); s2(0, 1);
+  }
+  return out;
+}
+
+// Build every gate of the table on the host (exact exponentiation) and upload it.
+int build_gates(tebd_ctx* c) {
+  const size_t DD = (size_t)c->D * c->D, L2 = (size_t)c->L - 2;
+  const std::vector<double> taus = gate_taus(c);
+  double2* G = dalloc<double2>(c, taus.size() * L2 * DD);
+  if (!G) return TEBD_ERR_OOM;
+  std::vector<std::complex<double>> Gall(taus.size() * L2 * DD), Gj;
+  for (size_t t = 0; t < taus.size(); ++t)
+    for (int j = 1; j <= c->L - 2; ++j) {
+      if (!build_gate(c->L, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t], Gj)) return TEBD_ERR_NOT_CONVERGED;
+      std::copy(Gj.begin(), Gj.end(), Gall.begin() + (t * L2 + (j - 1)) * DD);
+    }
+  if (cudaMemcpy(G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return TEBD_ERR_CUDA;
+  }
+  if (c->G) {  // replace the previous table
+    for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+      if (*it == c->G) { c->allocs.erase(it); break; }
+    cudaFree(c->G);
+  }
+  c->G = G;
+  return TEBD_OK;
 }
 
 int alloc_workspace(tebd_ctx* c) {
@@ -970,21 +1022,12 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
     c->d_status = dalloc<int>(c, 1);
     c->d_occ = dalloc<int>(c, L);
     c->d_bar = dalloc<unsigned int>(c, 4);
-    const size_t DD = (size_t)c->D * c->D;
-    c->G = dalloc<double2>(c, 2 * (size_t)(L - 2) * DD);
-    if (!c->dB || !c->dlam || !c->d_status || !c->d_occ || !c->d_bar || !c->G) throw std::bad_alloc();
-    std::vector<std::complex<double>> Gall(2 * (size_t)(L - 2) * DD), Gj;
-    for (int t = 0; t < 2; ++t)
-      for (int j = 1; j <= L - 2; ++j) {
-        const double tau = (t == 0) ? 0.5 * dt : dt;
-        if (!build_gate(L, n_max, U, J, J_NNN, K, j_c, j, tau, Gj)) {
-          tebd_destroy(c);
-          return TEBD_ERR_NOT_CONVERGED;
-        }
-        std::copy(Gj.begin(), Gj.end(), Gall.begin() + ((size_t)t * (L - 2) + (j - 1)) * DD);
-      }
-    if (cudaMemcpy(c->G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->dB, c->B.data(), L * sizeof(double2*), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (int r = build_gates(c)) {
+      tebd_destroy(c);
+      return r;
+    }
+    if (!c->dB || !c->dlam || !c->d_status || !c->d_occ || !c->d_bar) throw std::bad_alloc();
+    if (cudaMemcpy(c->dB, c->B.data(), L * sizeof(double2*), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->dlam, c->lam.data(), (L + 1) * sizeof(double*), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_bar, 0, 4 * sizeof(unsigned int)) != cudaSuccess) {
@@ -1013,6 +1056,16 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
   } else if (k == "precision") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return TEBD_ERR_ARG;
     h->precision = (int)value;
+  } else if (k == "trotter_order") {
+    if (value != 2.0 && value != 4.0) return TEBD_ERR_ARG;
+    if ((int)value != h->order) {
+      if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
+      h->order = (int)value;
+      if (int r = build_gates(h)) {
+        h->sticky = r;
+        return r;
+      }
+    }
   } else if (k == "profile") {
     if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
@@ -1088,11 +1141,11 @@ int tebd_step(tebd_handle h, int n_steps) {
   if (n_steps == 0) return TEBD_OK;
   try {
     if (int r = alloc_workspace(h)) return r;
-    // A(dt/2) B(dt/2) C(dt) B(dt/2) A(dt/2); residue r <-> triples j = r+1 mod 3
-    const int sched[5][2] = {{0, 0}, {1, 0}, {2, 1}, {1, 0}, {0, 0}};
+    // the layers of one step (residue r <-> triples j = r+1 mod 3, gate-table index)
+    const std::vector<std::pair<int, int>> layers = step_layers(h);
     for (int n = 0; n < n_steps; ++n) {
-      for (int l = 0; l < 5; ++l)
-        if (int r = run_layer(h, sched[l][0], sched[l][1])) return r;
+      for (const auto& l : layers)
+        if (int r = run_layer(h, l.first, l.second)) return r;
       h->steps += 1;
     }
   } catch (...) {
@@ -1128,7 +1181,8 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
     if (!hs[i]) return TEBD_ERR_ARG;
     if (hs[i]->sticky != TEBD_OK) return hs[i]->sticky;
     if (!hs[i]->have_state) return TEBD_ERR_STATE;
-    if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision) return TEBD_ERR_ARG;
+    if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision || hs[i]->order != hs[0]->order)
+      return TEBD_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return TEBD_ERR_ARG;
   }
@@ -1139,9 +1193,10 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
   try {
     for (tebd_ctx* h : v)
       if ((r = alloc_workspace(h)) != TEBD_OK) return r;
-    const int sched[5][2] = {{0, 0}, {1, 0}, {2, 1}, {1, 0}, {0, 0}};
+    const std::vector<std::pair<int, int>> layers = step_layers(c);
     for (int step = 0; step < n_steps && r == TEBD_OK; ++step) {
-      for (int l = 0; l < 5 && r == TEBD_OK; ++l) r = run_layer_multi(c, v, sched[l][0], sched[l][1]);
+      for (size_t l = 0; l < layers.size() && r == TEBD_OK; ++l)
+        r = run_layer_multi(c, v, layers[l].first, layers[l].second);
       if (r == TEBD_OK)
         for (tebd_ctx* h : v) h->steps += 1;
     }

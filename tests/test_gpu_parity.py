@@ -76,6 +76,32 @@ def test_exact_digit_precision_holds_fp64_bound(lib, name, steps, every):
     print(f"{name} exact-digit parity: max |delta| = {worst:.3e}")
 
 
+def test_fourth_order_split_matches_oracle(lib):
+    """trotter_order 4 (Suzuki's composition of the second-order step, 25 layers):
+    the GPU FP64 path against the oracle's fourth-order split, L=8, to t = 0.6."""
+    from paper_2401_05301_gb300 import TEBD
+    wl = workloads.PARITY_L8
+    args = dict(L=wl.L, n_max=wl.n_max, chi_max=wl.chi_max, U=wl.U, J=wl.J, Jnnn=wl.Jnnn, K=wl.K, jc=wl.jc,
+                dt=wl.dt, w_cut=wl.w_cut, eps_rel=wl.eps_rel)
+    g = TEBD(**args)
+    g.set_option("trotter_order", 4)
+    o = OracleTEBD(**args, order=4)
+    occ = wl.occupation()
+    g.init_product(occ)
+    o.init_product(occ)
+    worst = 0.0
+    for _ in range(6):
+        g.step(10)
+        o.step(10)
+        n_g, cur_g = g.measure()
+        worst = max(worst, np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+    t, _, _ = g.stats()
+    g.close()
+    print(f"fourth-order parity: max |delta| = {worst:.3e}")
+    assert abs(t - 60 * wl.dt) < 1e-12
+    assert worst < TOL
+
+
 def test_hard_core_free_fermions_on_gpu(lib):
     """n_max = 1, J_NNN = 0: the GPU run follows the Trotterised free-fermion propagator.
 
