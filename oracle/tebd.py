@@ -155,7 +155,8 @@ class TEBD:
 
     def step(self, n: int = 1):
         """n full steps of the Trotter split of the given order (model.step_schedule)."""
-        sched = model.step_schedule(self.L, self.dt, self.order)
+        sched = (model.step_schedule(self.L, self.dt) if self.order == 2
+                 else model.step_schedule(self.L, self.dt, self.order))
         for _ in range(n):
             for triples, tau in sched:
                 self.layer(triples, tau)
