@@ -87,6 +87,7 @@ class TEBD:
         self.t = 0.0
         self.steps = 0
         self.w_total = 0.0
+        self.min_cut_gap = float("inf")  # smallest (p_{chi'} - p_{chi'+1}) / p_{chi'} seen at a cut
 
     # -- gates -----------------------------------------------------------------
     def gate(self, j: int, tau: float) -> np.ndarray:
@@ -123,6 +124,8 @@ class TEBD:
     def _truncated_svd(self, M):
         U, s, Vh = svd_desc(M)
         k, w = truncation_rule(s, self.chi_max, self.w_cut, self.eps_rel)
+        if k < len(s):  # record how close the decision was: relative gap at the cut
+            self.min_cut_gap = min(self.min_cut_gap, float((s[k - 1] ** 2 - s[k] ** 2) / s[k - 1] ** 2))
         s = s[:k]
         norm = np.sqrt(np.sum(s * s))
         return s / norm, Vh[:k], norm, w

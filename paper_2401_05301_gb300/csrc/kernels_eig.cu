@@ -921,9 +921,17 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
   int launches = 0;
   for (int k0 = 0; k0 < mm; k0 += TD_NB) {
     int k1 = std::min(mm, k0 + TD_NB);
+    // grid sized to the panel's largest phase (its first column's slabs): small matrices
+    // get a small grid, whose barriers are cheaper; at least one block per matrix
+    long long items = 0;
+    for (int i = 0; i < b.n; ++i) {
+      const int n = b.a[i].m - k0 - 1;
+      if (n > 0) items += (long long)((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK);
+    }
+    const int gsz = (int)std::min<long long>(grid, std::max<long long>(b.n, items));
     cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
     void* args[] = {const_cast<EigBatch*>(&b), &k0, &k1};
-    if (cudaLaunchCooperativeKernel((const void*)k_tridiag_panel, dim3(grid), dim3(TD_THREADS), args, 0, s) !=
+    if (cudaLaunchCooperativeKernel((const void*)k_tridiag_panel, dim3(gsz), dim3(TD_THREADS), args, 0, s) !=
         cudaSuccess)
       return -1;
     ++launches;

@@ -38,8 +38,12 @@ def _compare_run(lib, wl, n_steps, every, **kw):
         n_o, cur_o = o.densities(), o.currents()
         err = max(np.max(np.abs(n_g - n_o)), np.max(np.abs(cur_g - cur_o)))
         chi_g, chi_o = list(g.bond_dims()), o.chi()
-        assert err < TOL, f"step {k}: max |dn|,|dcur| = {err:.3e}; chi gpu {chi_g} oracle {chi_o}"
+        differ = sum(int(a != b) for a, b in zip(chi_g, chi_o))
+        assert err < TOL, (f"step {k}: max |dn|,|dcur| = {err:.3e}; chi' differs on {differ} bonds "
+                           f"(gpu {chi_g} oracle {chi_o}); smallest relative gap at a cut so far "
+                           f"{o.min_cut_gap:.2e}" + ("  -> unpinned at a truncation tie" if differ else ""))
         worst = max(worst, err)
+    print(f"{wl.name}: smallest relative gap at a truncation cut {o.min_cut_gap:.2e}")
     t, w, _ = g.stats()
     assert abs(t - n_steps * wl.dt) < 1e-12
     assert abs(w - o.w_total) <= 1e-9 * max(1.0, o.w_total) + 1e-14

@@ -300,3 +300,27 @@ def test_fourth_order_tebd_matches_dense_trotter():
     n_d, C_d = ed.dense_observables(psi)
     assert np.max(np.abs(T.densities() - n_d)) < 1e-12
     assert np.max(np.abs(T.correlators() - C_d)) < 1e-12
+
+
+def test_synthetic_saturated_state_recipe():
+    """The timed input: right-canonical B_k (rows orthonormal as chi_k x d chi_{k+1}),
+    sum lambda^2 = 1, bond dimensions min(chi_max, d^min(k, L-k)), seeded."""
+    B, lam, chi = workloads.synthetic_state(12, 3, 20)
+    assert chi == [min(20, 3 ** min(k, 12 - k)) for k in range(13)]
+    for k, b in enumerate(B):
+        assert b.shape == (chi[k], 3, chi[k + 1])
+        M = b.reshape(chi[k], -1)
+        assert np.max(np.abs(M @ M.conj().T - np.eye(chi[k]))) < 1e-12
+    for x in lam:
+        assert abs(np.sum(x * x) - 1.0) < 1e-14 and np.all(np.diff(x) <= 0)
+    B2, lam2, _ = workloads.synthetic_state(12, 3, 20)
+    assert all(np.array_equal(a, b) for a, b in zip(B, B2))
+
+
+def test_oracle_records_the_closest_truncation_decision():
+    """min_cut_gap: relative gap p_chi' - p_chi'+1 at the tightest cut taken."""
+    T = TEBD(5, 1, 2, 1.0, 1.0, 0.0, 0.0, 3.0, 0.1)
+    T.init_product(workloads.cdw(5))
+    assert T.min_cut_gap == float("inf")
+    T.step(3)
+    assert 0.0 < T.min_cut_gap <= 1.0
