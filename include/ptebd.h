@@ -103,7 +103,7 @@ int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precis
  * layer, the triples of all simulations are processed as shared batches: each
  * stage of the local update is one grouped launch over all of them.  Work
  * runs on hs[0]'s stream; all handles must be on the same device, hold a
- * state and use the same "precision" (else TEBD_ERR_ARG).  Each simulation's
+ * state and use the same "precision" and "trotter_order" (else TEBD_ERR_ARG).  Each simulation's
  * result is bitwise the same as stepping it alone.  A device error marks every
  * member sticky. */
 int tebd_batch_step(tebd_handle* hs, int n, int n_steps);
@@ -111,7 +111,7 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps);
 /* Apply one Trotter layer only: every triple j = residue + 1 (mod 3), 1-based
  * (residue in {0, 1, 2}), with tau = dt/2 (full = 0) or dt (full = 1).  The
  * step counter and t are unchanged.  Used to compare single layers of large
- * states against a reference. */
+ * states against a reference.  Needs trotter_order 2 (else TEBD_ERR_ARG). */
 int tebd_layer(tebd_handle h, int residue, int full);
 
 /* Measure n_j (j = 1..L) into n_out[L] and current_j = 2 J Im <b+_j b_{j+1}>

@@ -1211,6 +1211,7 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
 int tebd_layer(tebd_handle h, int residue, int full) {
   CHECK_HANDLE(h);
   if (residue < 0 || residue > 2 || (full != 0 && full != 1)) return TEBD_ERR_ARG;
+  if (h->order != 2) return TEBD_ERR_ARG;  // the gate table holds dt/2 and dt only at order 2
   if (!h->have_state) return TEBD_ERR_STATE;
   try {
     if (int r = alloc_workspace(h)) return r;

@@ -998,23 +998,45 @@ int eig_vectors(const EigBatch& b0, bool mixed, void* const* oz_ws, int* status,
   bool in_z2 = false;
   for (int it = 0; it < 3; ++it) {
     Gemm g1(false, OP_C, OP_N), g2(false, OP_N, OP_N);
-    for (int i = 0; i < b.n; ++i) {
-      const EigMat& M = b.a[i];
-      if (M.K == 0) continue;
-      const double* Zc = in_z2 ? M.Z2 : M.Z;
-      g1.add(M.K, M.K, M.m, Zc, M.K, Zc, M.K, M.S, M.K);
-    }
-    launches += g1.launch(s);
-    k_ns_form<<<dim3(std::max(1, std::min(64, (Kmax * Kmax + 255) / 256)), b.n), 256, 0, s>>>(b);
-    ++launches;
+    std::vector<OzProb> o1, o2;  // the mixed path: the same real products on the exact-digit engine
     for (int i = 0; i < b.n; ++i) {
       const EigMat& M = b.a[i];
       if (M.K == 0) continue;
       const double* Zc = in_z2 ? M.Z2 : M.Z;
       double* Zn = in_z2 ? M.Z : M.Z2;
-      g2.add(M.m, M.K, M.K, Zc, M.K, M.S, M.K, Zn, M.K);
+      if (mixed) {
+        OzProb q{};
+        q.row_div = q.col_div = 1;
+        q.alpha = 1.0;
+        q.ws = oz_ws[i];
+        OzProb g = q;  // S = Z^T Z
+        g.a = OzOperand{reinterpret_cast<const double2*>(Zc), 1, M.K, nullptr, 1, 0, 1};
+        g.M = g.N = M.K; g.K = M.m; g.Creal = M.S; g.ldc = M.K; g.gram = g.herm = 1;
+        o1.push_back(g);
+        OzProb z = q;  // Z' = Z S
+        z.a = OzOperand{reinterpret_cast<const double2*>(Zc), M.K, 1, nullptr, 1, 0, 1};
+        z.b = OzOperand{reinterpret_cast<const double2*>(M.S), 1, M.K, nullptr, 1, 0, 1};
+        z.M = M.m; z.N = M.K; z.K = M.K; z.Creal = Zn; z.ldc = M.K;
+        o2.push_back(z);
+      } else {
+        g1.add(M.K, M.K, M.m, Zc, M.K, Zc, M.K, M.S, M.K);
+      }
     }
-    launches += g2.launch(s);
+    launches += mixed ? oz_gemm_launch(o1, status, s) : g1.launch(s);
+    k_ns_form<<<dim3(std::max(1, std::min(64, (Kmax * Kmax + 255) / 256)), b.n), 256, 0, s>>>(b);
+    ++launches;
+    if (mixed) {
+      launches += oz_gemm_launch(o2, status, s);
+    } else {
+      for (int i = 0; i < b.n; ++i) {
+        const EigMat& M = b.a[i];
+        if (M.K == 0) continue;
+        const double* Zc = in_z2 ? M.Z2 : M.Z;
+        double* Zn = in_z2 ? M.Z : M.Z2;
+        g2.add(M.m, M.K, M.K, Zc, M.K, M.S, M.K, Zn, M.K);
+      }
+      launches += g2.launch(s);
+    }
     in_z2 = !in_z2;
   }
   const int mm = max_m(b);

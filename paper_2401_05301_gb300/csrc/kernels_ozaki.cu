@@ -171,7 +171,8 @@ __device__ __forceinline__ uint32_t bf16_bits(int v) { return __float_as_uint((f
 
 // Element (r, k) of a job's operand, after the optional per-k scale and conjugation.
 __device__ __forceinline__ double2 job_elem(const OzPackJob& J, int r, int k) {
-  double2 x = J.X[(long long)r * J.rs + (long long)k * J.ks];
+  const long long at = (long long)r * J.rs + (long long)k * J.ks;
+  double2 x = J.real ? make_double2(reinterpret_cast<const double*>(J.X)[at], 0.0) : J.X[at];
   if (J.scale) {
     const double f = J.scale[k / J.scale_div];
     x.x *= f;
@@ -499,14 +500,20 @@ __global__ void __launch_bounds__(OZ_NT, 1) k_oz_gemm(const __grid_constant__ Oz
         double f = P.alpha;
         if (P.s_row) f *= P.s_row[i / P.row_div];
         if (P.s_col) f *= P.s_col[jj / P.col_div];
-        double2* dst = P.C + (long long)i * P.ldc + jj;
         double2 val = make_double2(stage[r * OZ_STAGE_LD + cc] * f, stage[r * OZ_STAGE_LD + OZ_TNC + cc] * f);
-        if (P.beta) {
-          const double2 old = *dst;
-          val.x += old.x;
-          val.y += old.y;
+        if (P.Creal) {  // real result (real operands): only the real part is stored
+          double* dst = P.Creal + (long long)i * P.ldc + jj;
+          if (P.beta) val.x += *dst;
+          *dst = val.x;
+        } else {
+          double2* dst = P.C + (long long)i * P.ldc + jj;
+          if (P.beta) {
+            const double2 old = *dst;
+            val.x += old.x;
+            val.y += old.y;
+          }
+          *dst = val;
         }
-        *dst = val;
         stage[r * OZ_STAGE_LD + cc] = val.x;  // the final value, for the mirror below
         stage[r * OZ_STAGE_LD + OZ_TNC + cc] = val.y;
       }
@@ -516,8 +523,10 @@ __global__ void __launch_bounds__(OZ_NT, 1) k_oz_gemm(const __grid_constant__ Oz
           const int cc = e / OZ_TM, r = e % OZ_TM;
           const int i = mt * OZ_TM + r, jj = nt * OZ_TNC + cc;
           if (i >= P.M || jj >= P.N || jj >= i) continue;
-          P.C[(long long)jj * P.ldc + i] =
-              make_double2(stage[r * OZ_STAGE_LD + cc], -stage[r * OZ_STAGE_LD + OZ_TNC + cc]);
+          if (P.Creal) P.Creal[(long long)jj * P.ldc + i] = stage[r * OZ_STAGE_LD + cc];
+          else
+            P.C[(long long)jj * P.ldc + i] =
+                make_double2(stage[r * OZ_STAGE_LD + cc], -stage[r * OZ_STAGE_LD + OZ_TNC + cc]);
         }
       }
     }
@@ -595,7 +604,7 @@ int oz_gemm_launch(const std::vector<OzProb>& probs, int* status, cudaStream_t s
       int* eB = gram ? eA : reinterpret_cast<int*>(ws + g.offEB);
       OzPackJob ja{};
       ja.X = p.a.X; ja.rs = p.a.rs; ja.ks = p.a.ks; ja.scale = p.a.scale; ja.scale_div = std::max(1, p.a.scale_div);
-      ja.conj = p.a.conj; ja.rows = p.M; ja.K = p.K; ja.nrb = g.nrbA; ja.nkt = g.nkt; ja.e = eA;
+      ja.conj = p.a.conj; ja.real = p.a.real; ja.rows = p.M; ja.K = p.K; ja.nrb = g.nrbA; ja.nkt = g.nkt; ja.e = eA;
       ja.P0 = DA; ja.type0 = 0;
       if (gram) {  // b = conj(a): D1 = digits of (ar, ai) = DA, D2 = (-ai, ar)
         ja.P1 = D2; ja.type1 = 3;
@@ -605,7 +614,7 @@ int oz_gemm_launch(const std::vector<OzProb>& probs, int* status, cudaStream_t s
       if (!gram) {
         OzPackJob jb{};
         jb.X = p.b.X; jb.rs = p.b.rs; jb.ks = p.b.ks; jb.scale = p.b.scale; jb.scale_div = std::max(1, p.b.scale_div);
-        jb.conj = p.b.conj; jb.rows = p.N; jb.K = p.K; jb.nrb = g.nrbB; jb.nkt = g.nkt; jb.e = eB;
+        jb.conj = p.b.conj; jb.real = p.b.real; jb.rows = p.N; jb.K = p.K; jb.nrb = g.nrbB; jb.nkt = g.nkt; jb.e = eB;
         jb.P0 = D1; jb.type0 = 1;
         jb.P1 = D2; jb.type1 = 2;
         add_job(eb, eblocks, jb, g.nrbB);
@@ -613,7 +622,7 @@ int oz_gemm_launch(const std::vector<OzProb>& probs, int* status, cudaStream_t s
       }
       OzTile& t = gb.p[gb.nprob];
       t.DA = DA; t.D1 = gram ? DA : D1; t.D2 = D2; t.eA = eA; t.eB = eB;
-      t.C = p.C; t.ldc = p.ldc; t.alpha = p.alpha; t.s_row = p.s_row; t.s_col = p.s_col;
+      t.C = p.C; t.Creal = p.Creal; t.ldc = p.ldc; t.alpha = p.alpha; t.s_row = p.s_row; t.s_col = p.s_col;
       t.row_div = std::max(1, p.row_div); t.col_div = std::max(1, p.col_div);
       t.M = p.M; t.N = p.N; t.nkt = g.nkt; t.nrbA = g.nrbA; t.nrbB = g.nrbB; t.herm = p.herm; t.beta = p.beta;
       t.tiles_n = (p.N + OZ_TNC - 1) / OZ_TNC;

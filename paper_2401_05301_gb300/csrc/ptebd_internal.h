@@ -73,6 +73,7 @@ struct OzOperand {
   long long rs, ks;
   const double* scale;  // optional factor along the reduction index
   int scale_div, conj;
+  int real;  // X holds real doubles (element (r, k) = X_real[r * rs + k * ks], imaginary part 0)
 };
 struct OzProb {
   OzOperand a, b;  // b is ignored when gram is set
@@ -86,6 +87,7 @@ struct OzProb {
   int herm;  // Hermitian result (M == N): only j <= i is computed, then mirrored
   int gram;  // b(j, k) = conj(a(j, k)), N = M: the digits of a serve both operands
   int beta;  // 1: C += result (for herm, the lower triangle is read), 0: C = result
+  double* Creal;  // if set, the real part of the result goes here (ldc in doubles) instead of C
   void* ws;  // oz_workspace_bytes(M, N, K, gram) bytes, 256-byte aligned, owned by the caller
 };
 constexpr int OZ_MAXP = 16;
@@ -93,7 +95,7 @@ struct OzPackJob {
   const double2* X;
   long long rs, ks;
   const double* scale;
-  int scale_div, conj, rows, K, nrb, nkt;
+  int scale_div, conj, rows, K, nrb, nkt, real;
   uint16_t* P0;  // digit plane written with form type0 (null: none)
   uint16_t* P1;
   int type0, type1;
@@ -111,6 +113,7 @@ struct OzTile {
   const int* eA;
   const int* eB;
   double2* C;
+  double* Creal;
   long long ldc;
   double alpha;
   const double* s_row;
