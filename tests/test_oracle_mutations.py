@@ -135,3 +135,57 @@ def test_catches_wrong_fourth_order_weights():
     finally:
         model.step_schedule = good
     assert np.max(np.abs(T.densities() - n_ex)) > 1e-3  # the correct split is within 2.3e-7 here
+
+
+def _two_boson_error(three_site_term, U=2.5, J=0.9):
+    """Distance of the closed-form two-boson levels (U +- sqrt(U^2 + 8 J^2))/2 from the
+    spectrum of the L = 3 term (the closed-form pin, in miniature)."""
+    ev = np.linalg.eigvalsh(three_site_term(1, 3, 2, U, J, 0.0, 0.0, 2.0))
+    r = np.sqrt(U * U + 8 * J * J)
+    return max(np.min(np.abs(ev - x)) for x in ((U + r) / 2, (U - r) / 2))
+
+
+def test_catches_doubled_interaction_read_into_both_builders():
+    """U n(n-1) instead of U/2 n(n-1), misread into eq. (1) itself: the Fock-basis split
+    pin cannot see a mistake both builders share; the closed-form spectrum does."""
+    def bad(j, L, n_max, U, J, Jnnn, K, jc):
+        return model.three_site_term(j, L, n_max, 2 * U, J, Jnnn, K, jc)
+    assert _two_boson_error(model.three_site_term) < 1e-12
+    assert _two_boson_error(bad) > 1e-2
+
+
+def test_catches_missing_sqrt_n_in_annihilator():
+    orig = model.local_ops
+
+    def bad_ops(n_max):
+        b, num, one = orig(n_max)
+        return (b != 0).astype(b.dtype), num, one
+    try:
+        model.local_ops = bad_ops
+        assert _two_boson_error(model.three_site_term) > 1e-2
+    finally:
+        model.local_ops = orig
+
+
+def test_catches_dropped_interaction():
+    """The on-site U term left out: the d = 3 chain is then (up to the n_max cap) free bosons,
+    whose densities from singly occupied sites equal the free-fermion ones, so the deviation
+    no longer falls by 4 per doubling of U."""
+    from oracle import free
+    orig = model.three_site_term
+
+    def bad(j, L, n_max, U, J, Jnnn, K, jc):
+        return orig(j, L, n_max, 0.0, J, Jnnn, K, jc)
+    L, occ = 8, workloads.cdw(8)
+    n_free, _ = free.observables(free.propagator(free.one_body_h(L, 1.0, 0.0, 0.0, 4.5), 0.5), occ)
+    devs = []
+    try:
+        model.three_site_term = bad
+        for U in (20.0, 40.0):
+            T = TEBD(L, 2, 256, U, 1.0, 0.0, 0.0, 4.5, 0.01, eps_rel=1e-14)
+            T.init_product(occ)
+            T.step(50)
+            devs.append(np.max(np.abs(T.densities() - n_free)))
+    finally:
+        model.three_site_term = orig
+    assert not (3.6 < devs[0] / devs[1] < 4.4), devs

@@ -222,6 +222,58 @@ def test_tebd_hard_core_is_free_fermions():
     assert np.max(np.abs(T.correlators() - C)) < 1e-11
 
 
+def test_two_boson_spectrum_closed_form():
+    """L = 3, J_NNN = K = 0: the single three-site term is the whole of eq. (1).  In the
+    two-boson sector, the states odd under reflection, (|200> - |002>)/sqrt2 and
+    (|110> - |011>)/sqrt2, span an invariant block [[U, -sqrt2 J], [-sqrt2 J, 0]]: U from
+    U/2 n(n-1) at n = 2, and sqrt2 J from b+ on a singly occupied site.  Its eigenvalues
+    (U +- sqrt(U^2 + 8 J^2))/2, with 0 (vacuum) and 0, +-sqrt2 J (one boson, open 3-site
+    chain), must all be in the spectrum.  A factor 2 on U or a missing sqrt(n) moves them."""
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        U, J = rng.uniform(0.5, 6.0), rng.uniform(0.3, 2.0)
+        for n_max in (2, 3):
+            h = model.three_site_term(1, 3, n_max, U, J, 0.0, 0.0, 2.0)
+            ev = np.linalg.eigvalsh(h)
+            r = np.sqrt(U * U + 8 * J * J)
+            for x in (0.0, np.sqrt(2) * J, -np.sqrt(2) * J, (U + r) / 2, (U - r) / 2):
+                assert np.min(np.abs(ev - x)) < 1e-12, (U, J, n_max, x)
+            # the vacuum and the one-boson levels fill the N <= 1 sectors exactly
+            # (basis order: site 1 slowest, as the three-site term's (s1, s2, s3))
+            n_tot = np.array([sum(c) for c in ed.full_basis(3, n_max)[0]])
+            for N, want in ((0, [0.0]), (1, [-np.sqrt(2) * J, 0.0, np.sqrt(2) * J])):
+                idx = np.flatnonzero(n_tot == N)
+                assert np.allclose(np.linalg.eigvalsh(h[np.ix_(idx, idx)]), want, atol=1e-12)
+
+
+def test_large_u_approaches_hard_core_as_inverse_u_squared():
+    """d = 3, J_NNN = K = 0: as U grows, doubly occupied states are admixed with amplitude
+    O(J/U) (Sec. II A: U -> infinity is the hard-core, free-fermion limit), so the largest
+    deviation of n_j from the free-fermion values over t <= 1 falls as (J/U)^2: a factor 4
+    per doubling of U.  The currents, which oscillate at frequency U, fall at the same rate
+    on average (16 from U = 20 to 80).  Without the interaction the deviation would not fall
+    at all; a mis-scaled one is caught by the closed-form spectrum above."""
+    L, dt = 8, 0.01
+    occ = workloads.cdw(L)
+    h1 = free.one_body_h(L, 1.0, 0.0, 0.0, 4.5)
+    dev_n, dev_c = [], []
+    for U in (20.0, 40.0, 80.0):
+        T = TEBD(L, 2, 256, U, 1.0, 0.0, 0.0, 4.5, dt, eps_rel=1e-14)
+        T.init_product(occ)
+        dn = dc = 0.0
+        for k in range(1, 11):
+            T.step(10)
+            n, C = free.observables(free.propagator(h1, 0.1 * k), occ)
+            dn = max(dn, np.max(np.abs(T.densities() - n)))
+            dc = max(dc, np.max(np.abs(T.currents() - 2 * C.imag)))
+        dev_n.append(dn)
+        dev_c.append(dc)
+    for a, b in zip(dev_n, dev_n[1:]):
+        assert 3.6 < a / b < 4.4, dev_n
+    assert 10.0 < dev_c[0] / dev_c[2] < 25.0, dev_c
+    assert 1e-3 < dev_n[0] < 2e-2  # the hard-core limit is approached, not already reached
+
+
 # -- truncation and invariants --------------------------------------------------------
 
 def test_invariants_with_truncation():
