@@ -457,6 +457,12 @@ constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
 constexpr int TD_NB = 32;      // columns per panel of the blocked reduction
 constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian product
+// A column whose largest off-diagonal entry lies below 2^-900 is taken as already
+// reduced (tau = 0).  The Gram matrices here have trace ~1, so such entries are far
+// below their rounding; they do arise, as rounding noise that each Gram product
+// squares, in empty regions of the chain, and once subnormal the scale 1/amax of
+// the reflector would overflow and turn the column into NaN.
+constexpr double REFL_FLUSH = 0x1p-900;
 
 
 // Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
@@ -507,6 +513,7 @@ __device__ void house_row_block(const EigMat& M, int k, double* sh, double2* sca
   double amax = 0.0;
   for (int r = threadIdx.x; r < n; r += blockDim.x) amax = fmax(amax, fmax(fabs(x[r].x), fabs(x[r].y)));
   amax = -block_min(-amax, sh);
+  if (amax < REFL_FLUSH) amax = 0.0;
   const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
   double s = 0.0;
   for (int r = 1 + threadIdx.x; r < n; r += blockDim.x) {
@@ -627,6 +634,7 @@ __device__ void phase1_regs(const EigMat& M, int k, int j, double* sh, double2* 
     return;
   }
   amax = -block_min(-amax, sh);
+  if (amax < REFL_FLUSH) amax = 0.0;
   const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
   double s2 = 0.0;
 #pragma unroll

@@ -71,6 +71,14 @@ def test_parity_L32_truncating(lib):
     print(f"L32 parity: max |delta| = {worst:.3e}")
 
 
+def test_paper_setup_flanked_cdw(lib):
+    """The paper's own setup (Sec. II C): L = 121, d = 5, flanked CDW of 27 bosons,
+    Table Ib set a (J_NNN < 0), dt = 0.05 pi/2, cuts w = eps = 1e-12, chi_max = 40
+    (the paper's smallest); eight steps, measured every second step."""
+    worst = _compare_run(lib, workloads.paper_run("a", 27, 40), 8, 2)
+    print(f"paper setup parity: max |delta| = {worst:.3e}")
+
+
 @pytest.mark.parametrize("name,steps,every", [("PARITY_L8", 400, 10), ("TRUNC_L32", 100, 10)])
 def test_exact_digit_precision_holds_fp64_bound(lib, name, steps, every):
     """precision 2: every large product (contractions, Gram, projection, reduction

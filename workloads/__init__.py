@@ -16,6 +16,8 @@ hbar = J = 1 units):
 * ``BATCH48``     48 simulations with seeded L, U, J_NNN, K, chi_max draws.
 * ``SERVE500``    500-request seeded Poisson stream (90% MIXED_L64-style,
                   10% L=100, d=4, chi_max=2048 jobs).
+* ``paper_run``   the paper's own setup: L=121, d=5, flanked CDW of N bosons,
+                  Table Ib parameters, dt = 0.05 pi/2, cuts 1e-12.
 
 ``synthetic_state`` builds the reproducible saturated state used to time the
 update "at chi_max": chi_j = min(chi_max, d^min(j, L-j)), right-canonical B
@@ -78,6 +80,39 @@ MIXED_L64 = Workload("mixed_L64_d5_chi1024", L=64, n_max=4, chi_max=1024, U=3.0,
 # step holds the chi_max = 1024, d = 5 local updates in about a minute of GPU time.
 SAMPLE_L16_D5 = Workload("sample_L16_d5_chi1024", L=16, n_max=4, chi_max=1024, U=3.0, J=1.0, Jnnn=0.1, K=0.003,
                          jc=8.5, dt=0.005, t_end=8.0, w_cut=0.0)
+
+
+def flanked_cdw(L: int, N: int) -> np.ndarray:
+    """Sec. II C's initial state: a CDW of N bosons in the middle of the chain with empty flanks.
+
+    The central site (1-based (L+1)/2, the paper's j = 0) is occupied, and so is every
+    second site out to N occupied sites; every site at odd distance from the centre and
+    both flanks are empty.  Needs L odd, N odd and 2N - 1 <= L.
+    """
+    if L % 2 == 0 or N % 2 == 0 or not (1 <= N and 2 * N - 1 <= L):
+        raise ValueError("flanked CDW needs L odd, N odd and 2N - 1 <= L")
+    c = (L - 1) // 2  # 0-based centre
+    occ = np.zeros(L, dtype=np.int64)
+    half = (N - 1) // 2
+    occ[c - 2 * half:c + 2 * half + 1:2] = 1
+    return occ
+
+
+# Table Ib's four parameter sets (U, J_NNN, K; J = 1), J_NNN passed into eq. (1) as printed.
+PAPER_PARAMS = {"a": (2.442, -0.12, 0.010), "b": (3.604, -0.08, 0.013),
+                "c": (5.167, -0.05, 0.017), "d": (9.910, -0.03, 0.029)}
+
+
+def paper_run(sim: str, N: int, chi_max: int, L: int = 121, n_steps: int = 100) -> Workload:
+    """A run as the paper sets it up (Sec. II C): L = 121 sites, trap centred on the middle
+    site, flanked CDW of N bosons, n_max = 4, dt = 0.05 pi/2, 100 steps, discarded-weight and
+    relative cuts 1e-12, measured after every step.  The paper's chi_max values are 40, 200,
+    1000 and 5000; its ensemble over N needs weights that exist only in a missing figure."""
+    U, Jnnn, K = PAPER_PARAMS[sim]
+    dt = 0.05 * np.pi / 2
+    return Workload(f"paper_{sim}_L{L}_N{N}_chi{chi_max}", L=L, n_max=4, chi_max=chi_max, U=U, J=1.0,
+                    Jnnn=Jnnn, K=K, jc=(L + 1) / 2, dt=dt, t_end=n_steps * dt, w_cut=1e-12,
+                    eps_rel=1e-12, measure_every=1, occ=tuple(int(x) for x in flanked_cdw(L, N)))
 
 
 def batch48(seed: int = SEED):
