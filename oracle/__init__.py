@@ -12,6 +12,8 @@ tebd    second-order TEBD on a Vidal Gamma-lambda MPS stored in B-form
 ed      exact diagonalisation: dense Trotterised evolution and the fixed-N sector
 free    U = 0 free bosons / hard-core free fermions: one-body propagators and
         the uniform-chain Bessel closed forms
+supersite  the paper's super-site scheme (pairs of sites, d_eff = d^2, NN gates,
+        one SVD per gate), the next variant after the three-site path
 
 Every function cites the passage of the paper (arXiv:2401.05301) it follows.
 Where the paper is silent, the reading taken is stated in the docstring.

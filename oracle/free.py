@@ -98,6 +98,45 @@ def trotter_propagator(L, J, Jnnn, K, jc, dt, n_steps) -> np.ndarray:
     return np.linalg.matrix_power(step, n_steps)
 
 
+def _super_bond_one_body(k, Lp, J, Jnnn, K, jc) -> np.ndarray:
+    """4 x 4 one-body matrix of super bond k (1-based) over physical sites 2k-1..2k+2 of a
+    chain of Lp (even) sites, in the super-site split of Sec. II B: the NN hop (2k, 2k+1)
+    and the NNN hops (2k-1, 2k+1), (2k, 2k+2) in full; the hop inside each super site and
+    its trap terms divided by the number of super bonds holding that super site (1 or 2)."""
+    L_eff = Lp // 2
+
+    def share(kk):
+        return sum(1 for b in (kk - 1, kk) if 1 <= b <= L_eff - 1)
+
+    h = np.zeros((4, 4))
+    h[1, 2] = h[2, 1] = -J
+    h[0, 2] = h[2, 0] = h[1, 3] = h[3, 1] = -Jnnn
+    for kk, (p0, p1) in ((k, (0, 1)), (k + 1, (2, 3))):
+        c = share(kk)
+        h[p0, p1] += -J / c
+        h[p1, p0] += -J / c
+        h[p0, p0] += 0.5 * K * (2 * kk - 1 - jc) ** 2 / c
+        h[p1, p1] += 0.5 * K * (2 * kk - jc) ** 2 / c
+    return h
+
+
+def supersite_trotter_propagator(Lp, J, Jnnn, K, jc, dt, n_steps) -> np.ndarray:
+    """One-body propagator (Lp x Lp, Lp even) of n_steps of the super-site split:
+    odd super bonds for dt/2, even ones for dt, odd ones for dt/2."""
+    L_eff = Lp // 2
+
+    def layer(parity, tau):
+        W = np.eye(Lp, dtype=np.complex128)
+        for k in range(1, L_eff):
+            if k % 2 == parity:
+                blk = scipy.linalg.expm(-1j * tau * _super_bond_one_body(k, Lp, J, Jnnn, K, jc))
+                W[2 * k - 2:2 * k + 2, :] = blk @ W[2 * k - 2:2 * k + 2, :]
+        return W
+
+    odd, even = layer(1, dt / 2), layer(0, dt)
+    return np.linalg.matrix_power(odd @ even @ odd, n_steps)
+
+
 def bessel_bulk(t, J=1.0):
     """Uniform NN chain, odd sites occupied, far from the edges (closed form).
 
