@@ -48,6 +48,20 @@ def test_host_gate_matches_oracle(lib, n_max, L, j):
         assert np.max(np.abs(G.conj().T @ G - np.eye(len(G)))) < 1e-13
 
 
+@pytest.mark.parametrize("sim,j", [("a", 1), ("d", 1), ("d", 60), ("d", 119)])
+def test_host_gate_paper_setup(lib, sim, j):
+    """The paper's setup (L = 121, d = 5, Table Ib, dt = 0.05 pi/2): at the chain ends the
+    trap puts up to K/2 60^2 n = 209 on the diagonal of a three-site term, so these gates
+    test the host eigen-solver far from the small-trap workloads."""
+    import workloads
+    wl = workloads.paper_run(sim, 27, 40)
+    for tau in (wl.dt / 2, wl.dt):
+        G = binding.gate_host(wl.L, wl.n_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, j, tau)
+        ref = model.gate(model.three_site_term(j, wl.L, wl.n_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc), tau)
+        assert np.max(np.abs(G - ref)) < 2e-13
+        assert np.max(np.abs(G.conj().T @ G - np.eye(len(G)))) < 1e-13
+
+
 def test_host_gate_rejects_bad_args(lib):
     out = np.empty(2 * 64 ** 2)
     ptr = out.ctypes.data_as(binding._P_double)
