@@ -5,13 +5,16 @@
 // Stages (each batched over all triples of a layer):
 //   1. Householder reduction H = Q T Q^+ with T real symmetric tridiagonal
 //      (reflectors H(k) = I - tau_k v_k v_k^+ with real beta_k, so the
-//      sub-diagonal is real), in one persistent cooperative launch.
-//   2. Bisection on (division-free) Sturm counts for the kmax largest eigenvalues of T.
+//      sub-diagonal is real), blocked: one cooperative launch per panel of 32
+//      columns plus a Hermitian rank-64 update of the trailing matrix.
+//   2. Multisection on (division-free) Sturm counts for the kmax largest eigenvalues of T.
 //   3. Inverse iteration for the K kept eigenvalues (one thread per
 //      eigenvector, LU with partial pivoting of T - lambda I), with
 //      Gram-Schmidt inside groups of nearly equal eigenvalues.
 //   4. Newton-Schulz orthonormalisation Z <- Z (3I - Z^T Z)/2, three rounds.
-//   5. Back-transformation U = Q Z, one block per pair of eigenvectors.
+//   5. Back-transformation U = Q Z: in blocks of 64 reflectors (compact WY
+//      form) in the tensor-core paths, reflector by reflector with 8
+//      eigenvectors per block in the FP64 path.
 // All reductions use a fixed order, so results are bitwise reproducible.
 #include "ptebd_internal.h"
 
