@@ -1,6 +1,10 @@
 // FP64-accurate complex GEMM on the bf16 tensor cores by exact digit splitting
-// (the Ozaki scheme), for the Gram matrices H = theta' theta'^+ and the
-// projections Y = U^+ theta' of the truncated SVD (Sec. II B) in the mixed path.
+// (the Ozaki scheme), for the dense products of the truncated SVD (Sec. II B) in
+// the tensor-core paths: the Gram matrices H = theta' theta'^+, the projections
+// Y = U^+ theta', the Hermitian rank-64 updates of the blocked reduction, the
+// blocks of the back-transformation and the Newton-Schulz products (real
+// operands, real results); with precision 2 also the contractions of theta and
+// the rebuilds.
 //
 // Representation.  Every operand row is given an exponent e (|x| < 2^e over the
 // row) and each real x of it becomes the integer F = round(x 2^(56-e)),
