@@ -55,6 +55,13 @@ def test_bond_terms_sum_to_eq1(L, n_max):
     assert np.max(np.abs(S - H)) < 1e-13
 
 
+def test_paper_sizes():
+    """Sec. II C: 121 sites plus one empty site give L_eff = 61 super sites of d_eff = 25 (n_max = 4)."""
+    assert supersite.padded_length(121) // 2 == 61
+    T = SuperSiteTEBD(121, 4, 40, 2.442, 1.0, -0.12, 0.01, 61.0, 0.05 * np.pi / 2)
+    assert (T.L_eff, T.de, len(T.h)) == (61, 25, 60)
+
+
 def test_schedule_gives_every_bond_dt_and_disjoint_layers():
     for L_eff in (2, 3, 6, 61):
         tot = {}

@@ -32,3 +32,15 @@ def test_paper_run_setup():
     assert wl.w_cut == wl.eps_rel == 1e-12
     assert wl.occupation()[60] == 1 and wl.occupation().sum() == 27
     assert wl.n_steps * wl.dt == pytest.approx(2.5 * np.pi)  # t = 5 pi/2, the paper's last time
+
+
+def test_paper_params_match_table_1b():
+    """workloads.PAPER_PARAMS against the printed Table I(b) (tests/golden): a flipped J_NNN sign
+    or swapped columns would fail here."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table_1b_parameters.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert [r[0] for r in rows] == ["a", "b", "c", "d"]
+    for sim, U, Jnnn, K, J in rows:
+        assert workloads.PAPER_PARAMS[sim] == (float(U), float(Jnnn), float(K))
+        assert float(J) == 1.0 == workloads.paper_run(sim, 27, 40).J
