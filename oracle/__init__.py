@@ -14,6 +14,8 @@ free    U = 0 free bosons / hard-core free fermions: one-body propagators and
         the uniform-chain Bessel closed forms
 supersite  the paper's super-site scheme (pairs of sites, d_eff = d^2, NN gates,
         one SVD per gate), the next variant after the three-site path
+u1      the three-site update with U(1)-symmetric decompositions (charge-labelled
+        bonds, block-by-block SVDs, rule T on the merged spectrum), as the paper runs it
 
 Every function cites the passage of the paper (arXiv:2401.05301) it follows.
 Where the paper is silent, the reading taken is stated in the docstring.
