@@ -36,8 +36,18 @@ class U1TEBD(TEBD):
         self.q = [np.array([int(occ[:k].sum())], dtype=np.int64) for k in range(self.L + 1)]
         self.block_work = [0.0, 0.0]  # [sum over splits of sum_blocks b^3, of m^3] (Gram sizes)
 
-    def set_state(self, B, lam):
-        raise NotImplementedError("the U(1) oracle starts from product states (charges are derived)")
+    def set_state(self, B, lam, q=None):
+        """Install a B-form state with its bond charge labels q[k] (boson count left of bond k,
+        one entry per Schmidt index); the tensors must vanish outside the allowed charges."""
+        if q is None:
+            raise ValueError("the U(1) oracle needs the bond charge labels")
+        super().set_state(B, lam)
+        self.q = [np.asarray(x, dtype=np.int64).copy() for x in q]
+        for k in range(self.L):
+            ok = self.q[k + 1][None, None, :] == self.q[k][:, None, None] + np.arange(self.d)[None, :, None]
+            if np.any(np.where(ok, 0.0, np.abs(self.B[k])) > 0.0):
+                raise ValueError(f"site {k}: entries outside the allowed charges")
+        self.block_work = [0.0, 0.0]
 
     def _block_svd(self, M, row_q, col_q):
         """Truncated SVD of M, block diagonal in charge: returns (s normalised, Vh rows, charges,

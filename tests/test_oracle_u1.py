@@ -97,3 +97,28 @@ def test_mutation_wrong_column_charge_is_caught(monkeypatch):
     T.init_product(workloads.cdw(6))
     with pytest.raises(AssertionError, match="outside the charge blocks"):
         T.step(2)
+
+
+def test_charge_labelled_synthetic_state():
+    """workloads.synthetic_state_u1: right-canonical charge blocks, labels from 0 to N, and one A-layer
+    update of three triples gives the same new spectra in the U(1) oracle as in the dense one."""
+    L, d, chi, N = 32, 4, 256, 16
+    B, lam, q = workloads.synthetic_state_u1(L, d, chi, N)
+    assert q[0].tolist() == [0] and q[L].tolist() == [N]
+    for k in range(L):
+        M = B[k].reshape(B[k].shape[0], -1)
+        assert np.max(np.abs(M @ M.conj().T - np.eye(M.shape[0]))) < 1e-12
+        assert len(q[k]) <= min(chi, d ** min(k, L - k)) and np.all(np.diff(q[k]) >= 0)
+        assert abs(np.sum(lam[k] ** 2) - 1.0) < 1e-14
+    wl = workloads.TRUNC_L32
+    u, o = U1TEBD(**_args(wl)), TEBD(**_args(wl))
+    u.set_state(B, lam, q)
+    o.set_state(B, lam)
+    for j in (1, 13, 25):
+        G = o.gate(j, wl.dt / 2)
+        u.apply_gate(j - 1, G)
+        o.apply_gate(j - 1, G)
+        for b in (j, j + 1):
+            assert len(u.lam[b]) == len(o.lam[b])
+            assert np.max(np.abs(u.lam[b] - o.lam[b])) < 1e-12
+    assert u.block_fraction() < 0.1

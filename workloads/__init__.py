@@ -23,6 +23,9 @@ hbar = J = 1 units):
 update "at chi_max": chi_j = min(chi_max, d^min(j, L-j)), right-canonical B
 from the QR of seeded complex Gaussian matrices, and lambda_j with
 p_k proportional to exp(-8 k / chi_j).
+``synthetic_state_u1`` is the same kind of state with U(1) charge labels
+(block-structured B, labels = boson count left of each bond), for a path that
+exploits particle-number conservation.
 """
 from __future__ import annotations
 
@@ -160,6 +163,80 @@ def synthetic_state(L: int, d: int, chi_max: int, seed: int = SEED, decay: float
         p = np.exp(-decay * np.arange(n) / max(n, 1))
         lam.append(np.sqrt(p / p.sum()))
     return B, lam, chi
+
+
+def _sector_counts(sites: int, n_max: int, N: int) -> np.ndarray:
+    """Number of occupation strings of `sites` sites (0..n_max each) with each total 0..N."""
+    c = np.zeros(N + 1, dtype=np.float64)
+    c[0] = 1.0
+    for _ in range(sites):
+        nxt = np.zeros_like(c)
+        for s in range(n_max + 1):
+            nxt[s:] += c[:N + 1 - s]
+        c = nxt
+    return c
+
+
+def synthetic_state_u1(L: int, d: int, chi_max: int, N: int, seed: int = SEED, decay: float = 8.0):
+    """Seeded saturated B-form state with U(1) charge labels: (B, lambda, q).
+
+    q[k] holds, for each Schmidt index of bond k, the boson count on the sites left of
+    the bond (sorted ascending, so each charge is one contiguous run); B_k[a, s, b] is
+    non-zero only where q[k+1][b] = q[k][a] + s, and each charge block of B_k has
+    orthonormal rows (right-canonical), from the QR of a seeded complex Gaussian block.
+    A charge c on bond k gets a share of chi_k = min(chi_max, d^min(k, L-k)) in
+    proportion to its largest possible Schmidt rank, capped so that the rows of every
+    block of B_k fit its columns.  lambda_k has p_i ~ exp(-decay i / chi_k), the largest
+    values on the charges nearest the mean filling N k / L.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_max = d - 1
+    if not (0 <= N <= L * n_max):
+        raise ValueError("N out of range")
+    chi = synthetic_bond_dims(L, d, chi_max)
+    sizes = [None] * (L + 1)
+    sizes[L] = {N: 1}
+    for k in range(L - 1, 0, -1):  # right to left, so the column counts of bond k+1 are known
+        left, right = _sector_counts(k, n_max, N), _sector_counts(L - k, n_max, N)
+        rank = {c: min(left[c], right[N - c]) for c in range(N + 1) if left[c] > 0 and right[N - c] > 0}
+        cols = {c: sum(sizes[k + 1].get(c + t, 0) for t in range(d)) for c in rank}
+        cap = {c: int(min(rank[c], cols[c])) for c in rank if min(rank[c], cols[c]) >= 1}
+        total = min(chi[k], sum(cap.values()))
+        weight = np.array([float(cap[c]) for c in sorted(cap)])
+        share = np.minimum(np.floor(total * weight / weight.sum()).astype(int), [cap[c] for c in sorted(cap)])
+        share = np.maximum(share, 0)
+        order = sorted(cap, key=lambda c: abs(c - N * k / L))
+        i = 0
+        while share.sum() < total:  # hand out the remainder, central charges first
+            c = order[i % len(order)]
+            j = sorted(cap).index(c)
+            if share[j] < cap[c]:
+                share[j] += 1
+            i += 1
+        sizes[k] = {c: int(n) for c, n in zip(sorted(cap), share) if n > 0}
+    sizes[0] = {0: 1}
+    q = [np.repeat(np.array(sorted(sz), dtype=np.int64), [sz[c] for c in sorted(sz)]) for sz in sizes]
+    B = []
+    for k in range(L):
+        a_n, b_n = len(q[k]), len(q[k + 1])
+        t = np.zeros((a_n, d, b_n), dtype=np.complex128)
+        for c in sizes[k]:
+            rows = np.flatnonzero(q[k] == c)
+            cols = [(s, b) for s in range(d) for b in np.flatnonzero(q[k + 1] == c + s)]
+            X = rng.standard_normal((len(cols), len(rows))) + 1j * rng.standard_normal((len(cols), len(rows)))
+            Q, _ = np.linalg.qr(X)
+            for ci, (s, b) in enumerate(cols):
+                t[rows, s, b] = Q[ci].conj()
+        B.append(t)
+    lam = []
+    for k in range(L + 1):
+        n = len(q[k])
+        p = np.exp(-decay * np.arange(n) / max(n, 1))
+        rank_order = np.argsort(np.abs(q[k] - N * k / L), kind="stable")
+        v = np.empty(n)
+        v[rank_order] = np.sqrt(p / p.sum())
+        lam.append(v)
+    return B, lam, q
 
 
 def random_product_states(L: int, n_max: int, count: int, seed: int = SEED):
