@@ -12,8 +12,9 @@ state with occupations occ_k
 The same formula holds for free fermions from a Slater product state, and
 hard-core bosons with nearest-neighbour hopping only map onto free fermions
 with no Jordan-Wigner string on NN terms; so for n_max = 1, J_NNN = 0 the
-densities and NN correlators of eq. (5), (8) follow it at any U (the paper's
-"U = 0, or equivalently U -> infinity" limit, Sec. III D).
+densities and NN correlators of eq. (5), (8) follow it at any U (Sec. III D
+treats the free and the infinitely repulsive chain as the same limit for these
+observables).
 
 A Trotterised gate exp(-i h_j tau) of a quadratic three-site term is a
 one-body 3 x 3 rotation, so the Trotterised one-body propagator reproduces a

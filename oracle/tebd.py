@@ -19,8 +19,9 @@ term acts), taken in the order the method states:
   6. R = diag(lam[i+1]) V1^+ as (chi' d) x (d chi_r); SVD, truncate, renormalise
   7. B_{i+1} = V1^+ V2 / ||s2||,  B_{i+2} = V2^+,  lam[i+2] = s2 / ||s2||
 
-Observables (Sec. II C, eqs. (5), (8)) are evaluated from the canonical form
-"assuming orthonormality" (Sec. II B), after every full step (reading O).
+Observables (Sec. II C, eqs. (5), (8)) are evaluated from the canonical form,
+taking the Schmidt bases as orthonormal without a full contraction (Sec. II B),
+after every full step (reading O).
 """
 from __future__ import annotations
 

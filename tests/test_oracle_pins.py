@@ -279,7 +279,7 @@ def test_large_u_approaches_hard_core_as_inverse_u_squared():
 def test_invariants_with_truncation():
     """chi_max = 8 forces truncation.  The contracted state keeps N exactly (the SVD
     respects U(1), Sec. II B) and norm 1 (renormalisation, Sec. II B); the canonical-form
-    densities ("assuming orthonormality") deviate from it only at O(w_total)."""
+    densities, which take the Schmidt bases as orthonormal, deviate from it only at O(w_total)."""
     L = 8
     T = TEBD(L, 3, 8, 5.0, 1.0, 0.12, 0.005, 4.5, 0.01, w_cut=1e-10, eps_rel=1e-12)
     T.init_product(workloads.cdw(L))
