@@ -415,7 +415,7 @@ def main():
                               "products as exact-digit tensor-core products); fp64_path: the plain FP64 GPU method on "
                               "the same state; exact_path: FP64-accurate throughout on the tensor cores"
                               if prec == 1 else "value: plain FP64 GPU method"),
-            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "value": value, "unit": UNIT, "svds_per_s": 2.0 * value, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+tf32x3",
             "data": "synthetic", "config": config(args.precision),
