@@ -133,6 +133,14 @@ def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def side_measurement(fn, *args):
+    """Run a measurement reported beside the headline; if it fails, record why instead of losing the line."""
+    try:
+        return fn(*args)
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def job_value(updates_per_rank: int, ws: int, seconds_max: float) -> float:
     """Whole-job throughput of ws replicas that each did updates_per_rank gate updates."""
     return updates_per_rank * ws / seconds_max
@@ -398,10 +406,10 @@ def main():
 
     served = None
     if not args.no_served and ws == 1:
-        served = served_measurement(stream.cuda_stream)
+        served = side_measurement(served_measurement, stream.cuda_stream)
     batched = None
     if not args.no_batched and ws == 1 and args.workload == "trunc_L32":
-        batched = batched_measurement(stream.cuda_stream)
+        batched = side_measurement(batched_measurement, stream.cuda_stream)
 
     cpu = None
     if not args.no_cpu_baseline:

@@ -63,3 +63,13 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_side_measurement_records_a_failure():
+    import bench
+
+    def boom(x):
+        raise RuntimeError(f"tebd_batch_step: non-finite singular values (status -7) {x}")
+    assert bench.side_measurement(lambda x: {"ok": x}, 3) == {"ok": 3}
+    assert bench.side_measurement(boom, 1) == {"error": "RuntimeError: tebd_batch_step: non-finite singular "
+                                                         "values (status -7) 1"}
