@@ -38,7 +38,7 @@ def test_strerror(lib):
     assert lib.tebd_strerror(-7) == b"non-finite singular values"
 
 
-@pytest.mark.parametrize("n_max,L,j", [(1, 5, 1), (2, 6, 2), (3, 8, 3), (3, 8, 6), (4, 64, 30)])
+@pytest.mark.parametrize("n_max,L,j", [(1, 5, 1), (2, 6, 2), (3, 8, 3), (3, 8, 6), (4, 64, 30), (7, 6, 2)])
 def test_host_gate_matches_oracle(lib, n_max, L, j):
     U, J, Jnnn, K, jc = 5.0, 1.0, 0.1, 0.003, (L + 1) / 2
     for tau in (0.005, 0.01):
