@@ -140,6 +140,22 @@ def test_brute_force_random_small(L):
         assert np.max(np.abs(T.correlators() - C_d)) < 1e-12
 
 
+def test_largest_local_dimension_matches_dense_trotter():
+    """n_max = 7 (d = 8, the library's largest; gates 512 x 512): L = 4 against the dense vector."""
+    L, n_max, dt = 4, 7, 0.05
+    T = TEBD(L, n_max, 10 ** 6, 2.0, 1.0, 0.15, 0.02, 2.5, dt, w_cut=0.0, eps_rel=1e-24)
+    occ = np.array([3, 0, 2, 1])
+    T.init_product(occ)
+    psi = ed.dense_product(occ, n_max + 1)
+    sched = model.step_schedule(L, dt)
+    for _ in range(6):
+        T.step()
+        psi = ed.dense_trotter_step(psi, T.gate, sched, n_max + 1)
+    n_d, C_d = ed.dense_observables(psi)
+    assert np.max(np.abs(T.densities() - n_d)) < 1e-12
+    assert np.max(np.abs(T.correlators() - C_d)) < 1e-12
+
+
 def test_trotter_error_is_second_order():
     """Exact sector ED vs TEBD at dt and dt/2: error ratio in [3.5, 4.5] (2nd order)."""
     wl = workloads.PARITY_L8
