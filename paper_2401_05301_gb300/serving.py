@@ -228,6 +228,8 @@ class Server:
                 else:
                     still.append(a)
             active = still
+        with self._lock:  # cancellations belong to this run's requests
+            self._cancel.clear()
         return results
 
 

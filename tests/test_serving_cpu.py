@@ -205,3 +205,11 @@ def test_budget_rounding_cannot_stall_admission():
                          estimate_fn=lambda L, n_max, chi, slots, precision: sizes[L])
     res = srv.run([_req(0, 0.0, 8, 2), _req(1, 0.0, 4, 2), _req(2, 0.0, 2, 2)])
     assert all(r.status == "ok" for r in res.values()) and log == [2, 2, 1, 1]
+
+
+def test_cancellations_do_not_outlive_their_run():
+    clock, log, created = FakeClock(), [], []
+    srv = _tracking_server(16.0, clock, log, created)
+    srv.cancel(0)
+    assert srv.run([_req(0, 0.0, 8, 2)])[0].status == "cancelled"
+    assert srv.run([_req(0, 0.0, 8, 2)])[0].status == "ok"  # the same id in a later run is served
