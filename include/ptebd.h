@@ -140,9 +140,9 @@ int tebd_get_site(tebd_handle h, int k, double* B, double* lam);
  * B_ptrs has L entries, lam_ptrs has L+1.  Resets t, steps and w_total.
  * Used to start from a saturated state.  The state is taken as given: the
  * method assumes the B-form of a normalised state (each B_k right-canonical,
- * sum_a lam_{k,a}^2 = 1), as every step leaves it; the eigen-solver treats
- * Gram entries below 2^-900 as zero, which is far below rounding only for such
- * a state. */
+ * sum_a lam_{k,a}^2 = 1), as a product state is and as each step keeps it up to
+ * its truncation; the eigen-solver treats Gram entries below 2^-900 as zero,
+ * which is far below rounding only for such a state. */
 int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs,
                    const double* const* lam_ptrs);
 
