@@ -105,9 +105,11 @@ class SectorED:
         self.c0 = self.V.conj().T @ psi0
 
     def state(self, t):
+        """psi(t) = V exp(-i E t) V^+ psi0 in the fixed-N sector (exact evolution under eq. (1))."""
         return self.V @ (np.exp(-1j * self.E * t) * self.c0)
 
     def observables(self, t):
+        """(n_j, C_j) of eqs. (8), (5) at time t."""
         return sector_observables(self.state(t), self.basis, self.index, self.L, self.n_max)
 
 
@@ -122,6 +124,7 @@ def apply_three_site(psi: np.ndarray, G: np.ndarray, i: int, d: int) -> np.ndarr
 
 
 def dense_product(occ, d):
+    """Product state |occ_1 ... occ_L> (eq. (2) form) as a dense array of shape (d,)*L."""
     L = len(occ)
     psi = np.zeros((d,) * L, dtype=np.complex128)
     psi[tuple(int(x) for x in occ)] = 1.0

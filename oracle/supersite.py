@@ -122,6 +122,7 @@ class SuperSiteTEBD:
         self.t, self.steps, self.w_total = 0.0, 0, 0.0
 
     def gate(self, k: int, tau: float) -> np.ndarray:
+        """exp(-i h_k tau) of super bond k (1-based), built once and cached (Sec. II B)."""
         key = (k, tau)
         if key not in self._gates:
             self._gates[key] = model.gate(self.h[k - 1], tau)
@@ -143,6 +144,7 @@ class SuperSiteTEBD:
         self.t, self.steps, self.w_total = 0.0, 0, 0.0
 
     def chi(self):
+        """Bond dimensions of the super-site chain, bonds 0..L_eff."""
         return [len(x) for x in self.lam]
 
     def apply_gate(self, i: int, G: np.ndarray):
@@ -167,6 +169,7 @@ class SuperSiteTEBD:
         return w
 
     def step(self, n: int = 1):
+        """n second-order steps of the NN split (odd bonds dt/2, even dt, odd dt/2)."""
         sched = step_schedule(self.L_eff, self.dt)
         for _ in range(n):
             for bonds, tau in sched:
@@ -177,6 +180,7 @@ class SuperSiteTEBD:
 
     # -- observables (eqs. (5), (8), canonical form) ----------------------------
     def _site_ops(self):
+        """b, b^+, n and 1 on one physical site (truncated Fock space, Sec. II B)."""
         b, num, one = model.local_ops(self.n_max)
         return b, b.conj().T, num, one
 

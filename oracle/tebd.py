@@ -119,10 +119,12 @@ class TEBD:
         self.lam = [np.array(x, dtype=np.float64) for x in lam]
 
     def chi(self):
+        """Bond dimensions chi_0..chi_L."""
         return [len(x) for x in self.lam]
 
     # -- local update ----------------------------------------------------------
     def _truncated_svd(self, M):
+        """SVD of M, cut by reading T and renormalised (reading R); returns (s, Vh, ||s_kept||, w)."""
         U, s, Vh = svd_desc(M)
         k, w = truncation_rule(s, self.chi_max, self.w_cut, self.eps_rel)
         if k < len(s):  # record how close the decision was: relative gap at the cut
@@ -154,6 +156,7 @@ class TEBD:
         return w1, w2
 
     def layer(self, triples, tau):
+        """One Trotter layer: the gates of the given (disjoint) triples for time tau."""
         for j in triples:
             self.apply_gate(j - 1, self.gate(j, tau))
 

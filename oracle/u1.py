@@ -31,6 +31,7 @@ class U1TEBD(TEBD):
     """Dense-storage TEBD whose truncated SVDs run block by block over U(1) charges."""
 
     def init_product(self, occ):
+        """Product state (eq. (2) form) with its bond charges: the boson count left of each bond."""
         super().init_product(occ)
         occ = np.asarray(occ, dtype=np.int64)
         self.q = [np.array([int(occ[:k].sum())], dtype=np.int64) for k in range(self.L + 1)]
