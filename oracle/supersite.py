@@ -19,7 +19,7 @@ super site (its NN hop (2k-1, 2k) and the on-site terms of its two sites) are
 shared equally among the one or two bonds that contain it, so that
 sum_k h_k equals eq. (1) exactly.  Second-order Trotter for a NN chain
 (Sec. II B): odd bonds for dt/2, even bonds for dt, odd bonds for dt/2.  One
-SVD per gate; the update is the B-form two-site update (Vidal, Sec. I B).
+SVD per gate; the update is the B-form two-site update of Vidal's TEBD (Sec. I).
 """
 from __future__ import annotations
 

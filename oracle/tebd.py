@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-State (Sec. I B, Vidal's TEBD; Sec. II B): B_k = Gamma_k lambda_k (right
+State (Vidal's TEBD, named in Sec. I; Sec. II B): B_k = Gamma_k lambda_k (right
 canonical) for sites k = 0..L-1 (0-based here), shape (chi_left, d, chi_right),
 and bond vectors lam[k] for k = 0..L, lam[k] sitting to the left of site k
 (lam[0] = lam[L] = [1]).

@@ -264,7 +264,7 @@ def test_two_boson_spectrum_closed_form():
 
 def test_large_u_approaches_hard_core_as_inverse_u_squared():
     """d = 3, J_NNN = K = 0: as U grows, doubly occupied states are admixed with amplitude
-    O(J/U) (Sec. II A: U -> infinity is the hard-core, free-fermion limit), so the largest
+    O(J/U) (Sec. III D: U -> infinity is the hard-core, free-fermion limit), so the largest
     deviation of n_j from the free-fermion values over t <= 1 falls as (J/U)^2: a factor 4
     per doubling of U.  The currents, which oscillate at frequency U, fall at the same rate
     on average (16 from U = 20 to 80).  Without the interaction the deviation would not fall
