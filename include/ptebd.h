@@ -74,7 +74,8 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
 int tebd_set_option(tebd_handle h, const char* key, double value);
 
 /* Issue all work on the given cudaStream_t (NULL = legacy default stream).
- * The stream must belong to the handle's device and outlive its use. */
+ * The stream must belong to the handle's device and outlive its use.
+ * Infrastructure: the paper has no counterpart. */
 int tebd_set_stream(tebd_handle h, void* cuda_stream);
 
 /* Reset the state to the product state |occ[0], ..., occ[L-1]> (eq. (2) form),
@@ -89,7 +90,8 @@ int tebd_init_product(tebd_handle h, const int* occ);
  * the new bond dimensions to size the next launches). */
 int tebd_step(tebd_handle h, int n_steps);
 
-/* Device bytes a handle with these sizes holds once stepped and measured
+/* Serving infrastructure (no counterpart in the paper): device bytes a handle
+ * with these sizes holds once stepped and measured
  * (state, gates, workspace for min(triples per layer, 24, max_slots > 0 ?
  * max_slots : 24) concurrent local updates, measurement buffers; precision 1
  * and 2 add the digit planes of the exact-digit products),
@@ -98,7 +100,8 @@ int tebd_step(tebd_handle h, int n_steps);
  * table is counted for trotter_order 2 (order 4 holds twice as many gates). */
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
-/* Batched form: advance n distinct handles (simulations with any L, n_max,
+/* Batched form (an addition: the paper runs one chain per job, Sec. II B, IV):
+ * advance n distinct handles (simulations with any L, n_max,
  * chi_max and parameters) by n_steps full steps together.  Within every
  * layer, the triples of all simulations are processed as shared batches: each
  * stage of the local update is one grouped launch over all of them.  Work
@@ -108,7 +111,8 @@ int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precis
  * member sticky. */
 int tebd_batch_step(tebd_handle* hs, int n, int n_steps);
 
-/* Apply one Trotter layer only: every triple j = residue + 1 (mod 3), 1-based
+/* Apply one layer of the second-order split of Sec. II B only: every triple
+ * j = residue + 1 (mod 3), 1-based
  * (residue in {0, 1, 2}), with tau = dt/2 (full = 0) or dt (full = 1).  The
  * step counter and t are unchanged.  Used to compare single layers of large
  * states against a reference.  Needs trotter_order 2 (else TEBD_ERR_ARG). */
@@ -125,10 +129,12 @@ int tebd_measure(tebd_handle h, double* n_out, double* cur_out);
  * dimension.  Any pointer may be NULL. */
 int tebd_stats(tebd_handle h, double* t, double* w_total, int* max_chi);
 
-/* Copy the bond dimensions chi_k, k = 0..L (chi_0 = chi_L = 1), into chi[L+1]. */
+/* Copy the bond dimensions chi_k, k = 0..L (chi_0 = chi_L = 1), into chi[L+1]:
+ * the MPS bond dimensions, capped by chi_max (Sec. II B). */
 int tebd_bond_dims(tebd_handle h, int* chi);
 
-/* Read back site k (0-based) as B[chi_k][d][chi_{k+1}] (complex FP64, real and
+/* Read back the B-form tensor B_k = Gamma_k lambda_k of Vidal's form (named in
+ * Sec. I) for site k (0-based) as B[chi_k][d][chi_{k+1}] (complex FP64, real and
  * imaginary interleaved: 2 * chi_k * d * chi_{k+1} doubles) and/or the bond
  * vector lambda_k (chi_k doubles, k = 0..L).  Host buffers owned by the caller,
  * sized from tebd_bond_dims; either pointer may be NULL. */
@@ -147,7 +153,8 @@ int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs,
                    const double* const* lam_ptrs);
 
 /* Number of local updates (three-site gates) applied since init, and the
- * number of CUDA kernels this handle has launched since create. */
+ * number of CUDA kernels this handle has launched since create.
+ * Infrastructure: the paper has no counterpart. */
 int tebd_counters(tebd_handle h, long long* gate_updates, long long* kernel_launches);
 
 /* Kernel classes timed when the option "profile" is 1. */
@@ -163,17 +170,18 @@ enum {
   TEBD_PROF_NCLASS = 8
 };
 
-/* Totals since the option "profile" was last set to 1: device time in ms (CUDA
+/* Infrastructure (no counterpart in the paper).  Totals since the option
+ * "profile" was last set to 1: device time in ms (CUDA
  * events on the handle's stream around each group of launches), kernel launches,
  * and algorithmic work (real FP64 flops for classes 0-5, with the Hermitian
  * Gram counted at half and the tridiagonal reduction at 16/3 m^3; bytes of the
  * site tensors read once for class 7).  Any output pointer may be NULL. */
 int tebd_profile(tebd_handle h, int cls, double* ms, long long* launches, double* work);
 
-/* Release everything the handle owns.  NULL is accepted. */
+/* Release everything the handle owns.  NULL is accepted.  Infrastructure. */
 void tebd_destroy(tebd_handle h);
 
-/* Static description of a status code. */
+/* Static description of a status code.  Infrastructure. */
 const char* tebd_strerror(int status);
 
 /* Host-only helper (no GPU needed): the FP64 gate exp(-i h_j tau) of triple
@@ -187,8 +195,8 @@ const char* tebd_strerror(int status);
 int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
                    int j, double tau, double* out);
 
-/* The complex contraction used by the local update, exposed for direct use and
- * testing: C = alpha * A * op(B) on device buffers (interleaved complex doubles,
+/* The complex contraction used by the local update of Sec. II B (theta, gate,
+ * rebuild), exposed for direct use and testing: C = alpha * A * op(B) on device buffers (interleaved complex doubles,
  * row-major with leading dimensions in complex elements), A: M x K, op(B): K x N
  * with opB = 0 (B stored K x N) or 1 (B^+, B stored N x K), C: M x N.
  * precision 0: FP64 on the CUDA cores; 1: split 3xTF32 on the tcgen05 tensor
