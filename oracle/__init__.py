@@ -16,6 +16,8 @@ supersite  the paper's super-site scheme (pairs of sites, d_eff = d^2, NN gates,
         one SVD per gate), the next variant after the three-site path
 u1      the three-site update with U(1)-symmetric decompositions (charge-labelled
         bonds, block-by-block SVDs, rule T on the merged spectrum), as the paper runs it
+randomized  truncation by a randomized range finder (the cheaper SVD of Sec. V),
+        test matrices passed in
 
 Every function cites the passage of the paper (arXiv:2401.05301) it follows.
 Where the paper is silent, the reading taken is stated in the docstring.

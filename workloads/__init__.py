@@ -239,6 +239,14 @@ def synthetic_state_u1(L: int, d: int, chi_max: int, N: int, seed: int = SEED, d
     return B, lam, q
 
 
+def gaussian_test_matrix(n: int, l: int, call: int, seed: int = SEED) -> np.ndarray:
+    """The n x l complex Gaussian test matrix of the call-th randomized decomposition:
+    drawn from its own stream, keyed by (seed, call), so every decomposition's draws are
+    fixed whatever ran before it."""
+    rng = np.random.Generator(np.random.PCG64([seed, 7, int(call)]))
+    return rng.standard_normal((n, l)) + 1j * rng.standard_normal((n, l))
+
+
 def random_product_states(L: int, n_max: int, count: int, seed: int = SEED):
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     return [rng.integers(0, n_max + 1, size=L) for _ in range(count)]
