@@ -70,6 +70,18 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
  *             S2(p dt)^2 S2((1-4p) dt) S2(p dt)^2 with p = 1/(4 - 4^(1/3)) (25 layers;
  *             the cross-check of Appendix A).  Changing it rebuilds the gate table
  *             (four time arguments instead of two) and synchronises the stream.
+ *   "jacobi_max_sweeps" sweep limit (1..1000, default 60) of the host Jacobi
+ *             eigen-solver that exponentiates the three-site terms; changing it
+ *             rebuilds the gate table, and a gate that does not converge within
+ *             the limit makes the call return TEBD_ERR_NOT_CONVERGED (sticky).
+ *   "wait_limit_clocks" limit, in GPU clock ticks (default 2e9, about 1 s), of
+ *             every grid-barrier wait of the cooperative tridiagonal reduction.
+ *             A wait that runs out records the failure, every block of the
+ *             launch leaves, and the step returns TEBD_ERR_TIMEOUT (sticky); the
+ *             CUDA context stays usable.  A diagnostic for the failure path: any
+ *             limit far below the default makes a step fail.  (The mbarrier waits
+ *             of the tensor-core kernels keep their fixed ~1 s limit, since one of
+ *             them guards the release of tensor memory.)
  * Unknown key or out-of-range value: TEBD_ERR_ARG. */
 int tebd_set_option(tebd_handle h, const char* key, double value);
 
@@ -195,6 +207,13 @@ const char* tebd_strerror(int status);
 int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
                    int j, double tau, double* out);
 
+/* tebd_gate_host with an explicit sweep limit (max_sweeps >= 1) for the host
+ * Jacobi eigen-solver.  The gate built from the sweeps done is written to out
+ * either way; TEBD_ERR_NOT_CONVERGED if the off-diagonal weight did not fall
+ * below 1e-32 of the Frobenius norm within max_sweeps.  Host only. */
+int tebd_gate_host_sweeps(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
+                          int j, double tau, int max_sweeps, double* out);
+
 /* The complex contraction used by the local update of Sec. II B (theta, gate,
  * rebuild), exposed for direct use and testing: C = alpha * A * op(B) on device buffers (interleaved complex doubles,
  * row-major with leading dimensions in complex elements), A: M x K, op(B): K x N
@@ -227,12 +246,18 @@ int tebd_zgemm(int precision, int opB, int M, int N, int K, double alpha, const 
  * larger sizes return TEBD_ERR_TOO_LARGE (with a message on stderr) and
  * launch nothing.
  * Memory: no cudaMalloc, cudaFree or other allocation.  Scratch is a fixed
- * file-scope device array of about 1.2 MB, held by every GPU that loads the
- * library until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current;
- * make this first call before any stream capture.  All calls on a device
- * share the array, so calls that overlap on the GPU (different streams, or
- * threads without ordering) race and give wrong results; serialise them. */
+ * file-scope device array of 1,179,648 bytes, held by every GPU that loads the
+ * library until the process exits.  Every call looks up that array's device
+ * address (cudaGetSymbolAddress) in the context current on the calling
+ * thread, so the address stays right after cudaDeviceReset or under another
+ * context; the first call in a context loads the library's device code there,
+ * so make it before any stream capture.  All calls on a device share the
+ * array, so calls that overlap on the GPU (different streams, or threads
+ * without ordering) race and give wrong results; serialise them.
+ * Errors: a CUDA error already pending when the call starts (left by other
+ * work) is reported as TEBD_ERR_CUDA without clearing it, and nothing is
+ * launched; otherwise TEBD_ERR_CUDA reports a failure of this call's own
+ * launches. */
 int tebd_bond_correlator_noalloc(const double* B_left, const double* lam_left, const double* B_right,
                                  int chi_l, int chi_m, int chi_r, int d, double* C_out, void* cuda_stream);
 

@@ -46,6 +46,8 @@ SIGNATURES = {
                                              _c_void_p, _c_void_p]),
     "tebd_gate_host": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double, _c_int,
                                 _c_double, _P_double]),
+    "tebd_gate_host_sweeps": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
+                                       _c_int, _c_double, _c_int, _P_double]),
 }
 
 _LIB = None
@@ -100,6 +102,16 @@ def gate_host(L, n_max, U, J, Jnnn, K, jc, j, tau) -> np.ndarray:
     d = n_max + 1
     out = np.empty(2 * d ** 6, dtype=np.float64)
     _check(load().tebd_gate_host(L, n_max, U, J, Jnnn, K, jc, j, tau, _dptr(out)), "tebd_gate_host")
+    return out.view(np.complex128).reshape(d ** 3, d ** 3)
+
+
+def gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, max_sweeps) -> np.ndarray:
+    """tebd_gate_host with a sweep limit for the host Jacobi solver; raises TEBDError
+    (status TEBD_ERR_NOT_CONVERGED) when the solver did not converge in time."""
+    d = n_max + 1
+    out = np.empty(2 * d ** 6, dtype=np.float64)
+    _check(load().tebd_gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, int(max_sweeps), _dptr(out)),
+           "tebd_gate_host_sweeps")
     return out.view(np.complex128).reshape(d ** 3, d ** 3)
 
 

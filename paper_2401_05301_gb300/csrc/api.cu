@@ -48,6 +48,8 @@ struct tebd_ctx {
   double w_cut = 0.0, eps_rel = 1e-12;
   int precision = 0, max_slots = 0;
   int order = 2;  // Trotter order: 2 or 4 (gate table and layer schedule follow it)
+  int jacobi_sweeps = 60;  // sweep limit of the host gate builder's Jacobi eigen-solver
+  long long wait_clocks = 2000000000LL;  // limit of each grid-barrier wait in the reduction (~1 s)
   cudaStream_t stream = nullptr;
   int device = 0;
   int sticky = TEBD_OK;
@@ -266,7 +268,8 @@ int build_gates(tebd_ctx* c) {
   std::vector<std::complex<double>> Gall(taus.size() * L2 * DD), Gj;
   for (size_t t = 0; t < taus.size(); ++t)
     for (int j = 1; j <= c->L - 2; ++j) {
-      if (!build_gate(c->L, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t], Gj)) return TEBD_ERR_NOT_CONVERGED;
+      if (!build_gate(c->L, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t], Gj, c->jacobi_sweeps))
+        return TEBD_ERR_NOT_CONVERGED;
       std::copy(Gj.begin(), Gj.end(), Gall.begin() + (t * L2 + (j - 1)) * DD);
     }
   if (cudaMemcpy(G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -382,6 +385,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   void* oz_ws[EIG_MAXP] = {};
   eb.n = (int)ts.size();
   eb.bar = c->d_bar;
+  eb.wait_clocks = c->wait_clocks;
   for (size_t t = 0; t < ts.size(); ++t) {
     const Slot& S = ts[t].h->slots[ts[t].slot];
     EigMat& M = eb.a[t];
@@ -984,6 +988,21 @@ int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K,
   return TEBD_OK;
 }
 
+int tebd_gate_host_sweeps(int L, int n_max, double U, double J, double J_NNN, double K, double j_c, int j,
+                          double tau, int max_sweeps, double* out) {
+  if (L < 3 || n_max < 1 || n_max > 7 || j < 1 || j > L - 2 || !out || max_sweeps < 1) return TEBD_ERR_ARG;
+  if (!is_fin(U) || !is_fin(J) || !is_fin(J_NNN) || !is_fin(K) || !is_fin(j_c) || !is_fin(tau)) return TEBD_ERR_ARG;
+  try {
+    std::vector<std::complex<double>> G;
+    const bool ok = build_gate(L, n_max, U, J, J_NNN, K, j_c, j, tau, G, max_sweeps);
+    std::memcpy(out, G.data(), G.size() * sizeof(std::complex<double>));
+    if (!ok) return TEBD_ERR_NOT_CONVERGED;
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return TEBD_OK;
+}
+
 int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K, double j_c, double dt,
                 tebd_handle* out) {
   if (!out) return TEBD_ERR_ARG;
@@ -1076,6 +1095,19 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
       h->prof_launches[q] = 0;
       h->prof_work[q] = 0.0;
     }
+  } else if (k == "jacobi_max_sweeps") {
+    if (value < 1 || value > 1000 || value != std::floor(value)) return TEBD_ERR_ARG;
+    if ((int)value != h->jacobi_sweeps) {
+      if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
+      h->jacobi_sweeps = (int)value;
+      if (int r = build_gates(h)) {
+        h->sticky = r;
+        return r;
+      }
+    }
+  } else if (k == "wait_limit_clocks") {
+    if (value < 0 || value > 1e12 || value != std::floor(value)) return TEBD_ERR_ARG;
+    h->wait_clocks = (long long)value;
   } else if (k == "max_slots") {
     if (value < 0 || value > MAX_SLOTS || value != std::floor(value)) return TEBD_ERR_ARG;
     if (!h->slots.empty()) return TEBD_ERR_STATE;

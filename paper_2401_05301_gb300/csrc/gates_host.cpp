@@ -35,13 +35,13 @@ int triples_with_site(int k, int L) {  // site k, 1-based
 // On return E holds the eigenvalues and V (row-major) the eigenvectors as
 // columns.  Each rotation first removes the phase of a_pq, then applies the
 // real rotation that zeroes it.
-bool hermitian_jacobi(int n, std::vector<cd>& A, std::vector<double>& E, std::vector<cd>& V) {
+bool hermitian_jacobi(int n, std::vector<cd>& A, std::vector<double>& E, std::vector<cd>& V, int max_sweeps) {
   V.assign((size_t)n * n, cd(0, 0));
   for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
   double fro = 0;
   for (auto& x : A) fro += std::norm(x);
   bool converged = false;
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double off = 0;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) off += std::norm(A[(size_t)p * n + q]);
@@ -119,12 +119,12 @@ std::vector<cd> three_site_term(int L, int n_max, double U, double J, double Jnn
 }
 
 bool build_gate(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int j,
-                double tau, std::vector<cd>& G) {
+                double tau, std::vector<cd>& G, int max_sweeps) {
   const int d = n_max + 1, D = d * d * d;
   std::vector<cd> h = three_site_term(L, n_max, U, J, Jnnn, K, jc, j);
   std::vector<double> E;
   std::vector<cd> V;
-  bool ok = hermitian_jacobi(D, h, E, V);
+  bool ok = hermitian_jacobi(D, h, E, V, max_sweeps);
   G.assign((size_t)D * D, cd(0, 0));
   std::vector<cd> ph(D);
   for (int k = 0; k < D; ++k) ph[k] = std::exp(cd(0, -E[k] * tau));

@@ -472,9 +472,10 @@ constexpr double REFL_FLUSH = 0x1p-900;
 // Every block adds 1 to the count with a fire-and-forget release reduction
 // (no serialised round trips) and polls it with acquire loads until it reaches
 // the next multiple of the grid size (`target`, advanced by each call).  Waits
-// at most ~1 s (2e9 clocks); on timeout it records the failure in st[2] and
-// returns false so every block can leave.  The count starts at 0 per launch.
-__device__ bool grid_sync(unsigned int* st, unsigned int& target) {
+// at most `limit` clocks (2e9, ~1 s, unless the handle's "wait_limit_clocks"
+// says otherwise); on timeout it records the failure in st[2] and returns
+// false so every block can leave.  The count starts at 0 per launch.
+__device__ bool grid_sync(unsigned int* st, unsigned int& target, long long limit) {
   __shared__ int ok_sh;
   __syncthreads();
   target += gridDim.x;
@@ -489,7 +490,7 @@ __device__ bool grid_sync(unsigned int* st, unsigned int& target) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(st) : "memory");
       if ((int)(v - target) >= 0) break;
       if (*verr) { ok = 0; break; }
-      if (clock64() - t0 > 2000000000LL) { atomicExch(st + 2, 1u); ok = 0; break; }
+      if (clock64() - t0 > limit) { atomicExch(st + 2, 1u); ok = 0; break; }
     }
     __threadfence();
     ok_sh = ok && (*verr == 0);
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
         WVm[(size_t)r * 2 * TD_NB + TD_NB + j] = v;
       }
     }
-    if (!grid_sync(b.bar, target)) return;
+    if (!grid_sync(b.bar, target, b.wait_clocks)) return;
     // ---- phase 2: h = A(k0) v by slabs.  Item (s, q) covers strip s (32 columns) and
     // chunk q (TD_CHUNK indices) of the trailing set: the column part reads the stored
     // rows r in chunk q above the strip's columns (r <= c, used as conj(A[r][c]) v[r]),
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
       }
       __syncthreads();
     }
-    if (!grid_sync(b.bar, target)) return;
+    if (!grid_sync(b.bar, target, b.wait_clocks)) return;
     // ---- phase 3: corrections, tau, the strip partials of p^+ v, and row k+1
     for (int item = blockIdx.x;; item += gridDim.x) {
       int rem = item, mi = -1;
@@ -893,7 +894,7 @@ __global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_const
       }
       __syncthreads();
     }
-    if (!grid_sync(b.bar, target)) return;
+    if (!grid_sync(b.bar, target, b.wait_clocks)) return;
   }
   // w of the panel's last column
   for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {

@@ -7,14 +7,13 @@
 // allocator must own every device byte, and latency-critical loops where a
 // cudaMalloc would synchronise the device.  tebd_bond_correlator_noalloc
 // serves them: the caller passes device inputs and a device output, and the
-// scratch lives in a file-scope __device__ array of fixed size
-// (NOALLOC_SCRATCH_BYTES, about 1.2 MB), which every GPU that loads the
-// library holds until the process exits.
+// scratch lives in a file-scope __device__ array of NOALLOC_SCRATCH_BYTES
+// (1,179,648 bytes), which every GPU that loads the library holds until the
+// process exits.
 #include "ptebd.h"
 #include "ptebd_internal.h"
 
 #include <cstdio>
-#include <mutex>
 
 using namespace ptebd;
 
@@ -25,33 +24,28 @@ constexpr int NA_MAX_D = 8;     // largest local dimension accepted (n_max <= 7)
 constexpr size_t NA_BIG = (size_t)NA_MAX_CHI * NA_MAX_D * NA_MAX_CHI;  // P' and Q' (complex elements)
 constexpr size_t NA_SMALL = (size_t)NA_MAX_CHI * NA_MAX_CHI;           // X and Y^T
 constexpr size_t NA_TOTAL = 2 * NA_BIG + 2 * NA_SMALL;
+constexpr size_t NOALLOC_SCRATCH_BYTES = NA_TOTAL * sizeof(double2);
 
 // Shared by every call on a device; calls that overlap on the GPU race on it.
 static __device__ __align__(256) double2 g_noalloc_scratch[NA_TOTAL];
+static_assert(sizeof(g_noalloc_scratch) == NOALLOC_SCRATCH_BYTES, "scratch size");
+static_assert(NOALLOC_SCRATCH_BYTES == 1179648, "the documented scratch size");
 
-constexpr int NA_MAX_DEVICES = 64;
-double2* g_scratch_ptr[NA_MAX_DEVICES] = {};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device.  The host-side
-// symbol g_noalloc_scratch is only a stand-in: a kernel must be given the
-// address cudaGetSymbolAddress returns with the device current.
-int scratch_for_current_device(double2** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
-    cudaGetLastError();
+// Device address of the scratch array in the context current on the calling
+// thread.  The host-side symbol g_noalloc_scratch is only a stand-in: a kernel
+// must be given the address cudaGetSymbolAddress returns with the device
+// current.  The address is looked up on every call rather than cached per
+// device ordinal: after cudaDeviceReset, or with another context current on
+// the same device, the library's device code is loaded again at a different
+// address, and a cached pointer would then point at memory this call does
+// not own.  The first lookup in a context loads the module there.
+int scratch_in_current_context(double2** out) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();  // no error was pending on entry, so this clears only our own
     return TEBD_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return TEBD_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<double2*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double2*>(p);
   return TEBD_OK;
 }
 
@@ -69,8 +63,11 @@ extern "C" int tebd_bond_correlator_noalloc(const double* B_left, const double* 
                  chi_l, chi_m, chi_r, d, NA_MAX_CHI, NA_MAX_D);
     return TEBD_ERR_TOO_LARGE;
   }
+  // An error left pending by earlier work (another library, or a kernel that
+  // faulted) belongs to its owner: report it without clearing it and launch nothing.
+  if (cudaPeekAtLastError() != cudaSuccess) return TEBD_ERR_CUDA;
   double2* scratch = nullptr;
-  if (int r = scratch_for_current_device(&scratch)) return r;
+  if (int r = scratch_in_current_context(&scratch)) return r;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const double2* Bl = reinterpret_cast<const double2*>(B_left);
   const double2* Br = reinterpret_cast<const double2*>(B_right);
@@ -95,6 +92,7 @@ extern "C" int tebd_bond_correlator_noalloc(const double* B_left, const double* 
   py.K = d * chi_r;
   gemm_launch_single(true, OP_N, OP_C, py, s);
   launch_trace_product(X, Yt, chi_m, reinterpret_cast<double2*>(C_out), s);
+  // only this call's launches can have set the error read here
   if (cudaGetLastError() != cudaSuccess) return TEBD_ERR_CUDA;
   return TEBD_OK;
 }

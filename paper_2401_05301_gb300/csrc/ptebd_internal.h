@@ -13,8 +13,9 @@ namespace ptebd {
 // ---- host gate builder (gates_host.cpp) --------------------------------------
 std::vector<std::complex<double>> three_site_term(int L, int n_max, double U, double J, double Jnnn,
                                                   double K, double jc, int j);
+// max_sweeps: limit of the cyclic Jacobi eigen-solver (false if it did not converge).
 bool build_gate(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int j,
-                double tau, std::vector<std::complex<double>>& G);
+                double tau, std::vector<std::complex<double>>& G, int max_sweeps = 60);
 
 // ---- grouped GEMM (kernels_gemm.cu) ------------------------------------------
 // C = alpha * op(A) * op(B) [+ C], op in {N, C = conjugate transpose, CJ = conjugate}; complex
@@ -174,6 +175,7 @@ struct EigBatch {
   EigMat a[EIG_MAXP];
   int n;
   unsigned int* bar;  // grid-barrier state {count, generation, error} for the persistent reduction
+  long long wait_clocks;  // limit of each grid-barrier wait of the reduction (clock64 ticks)
 };
 
 constexpr int EIG_PARTS = 384;  // partial sums of p^+ v, one per strip of 32 columns (m <= 12288)

@@ -68,3 +68,19 @@ def test_host_gate_rejects_bad_args(lib):
     assert lib.tebd_gate_host(2, 3, 1, 1, 0, 0, 1, 1, 0.1, ptr) == -1   # L < 3
     assert lib.tebd_gate_host(8, 3, 1, 1, 0, 0, 1, 7, 0.1, ptr) == -1   # j > L-2
     assert lib.tebd_gate_host(8, 3, float("nan"), 1, 0, 0, 1, 1, 0.1, ptr) == -1
+
+
+def test_host_jacobi_sweep_limit_reports_not_converged(lib):
+    """The host eigen-solver's sweep limit: one cyclic sweep cannot diagonalise a
+    64 x 64 three-site term to 1e-32 of its norm, so the call reports
+    TEBD_ERR_NOT_CONVERGED; with the default limit the same gate is built and
+    equals tebd_gate_host."""
+    L, n_max, U, J, Jnnn, K, jc, j, tau = 8, 3, 5.0, 1.0, 0.1, 0.003, 4.5, 3, 0.01
+    with pytest.raises(binding.TEBDError) as e:
+        binding.gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, 1)
+    assert e.value.status == -5
+    G = binding.gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, 60)
+    assert np.array_equal(G, binding.gate_host(L, n_max, U, J, Jnnn, K, jc, j, tau))
+    out = np.empty(2 * 64 ** 2)
+    assert lib.tebd_gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, 0,
+                                     out.ctypes.data_as(binding._P_double)) == -1
