@@ -65,6 +65,15 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
  *             2 = FP64-accurate throughout: the contractions too as exact-digit
  *             tensor-core products (the small gate product on FP64 CUDA cores)
  *   "max_slots" cap on triples processed concurrently (0 = automatic)
+ *   "u1"      0 (default): dense local updates; 1: the particle-number blocked
+ *             form of Sec. II B's U(1)-symmetric tensors.  Every gate conserves
+ *             N, so each Schmidt vector carries a charge (tebd_set_charges) and
+ *             the contractions and both truncated SVDs run block by block over
+ *             the charges; rule T is applied to the merged spectrum of all blocks
+ *             of a cut, and the kept vectors are stored sorted by charge.  The
+ *             site tensors stay dense in device memory (zero outside their
+ *             blocks), so measurement and state I/O are unchanged.  Valid before
+ *             the first step only (TEBD_ERR_STATE afterwards).
  *   "trotter_order" 2 (default): the symmetric step A(dt/2) B(dt/2) C(dt) B(dt/2)
  *             A(dt/2); 4: Suzuki's fourth-order composition of that step,
  *             S2(p dt)^2 S2((1-4p) dt) S2(p dt)^2 with p = 1/(4 - 4^(1/3)) (25 layers;
@@ -163,6 +172,24 @@ int tebd_get_site(tebd_handle h, int k, double* B, double* lam);
  * which is far below rounding only for such a state. */
 int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs,
                    const double* const* lam_ptrs);
+
+/* Bond charges for the particle-number (U(1)) blocked form of the option "u1"
+ * (the paper's U(1)-symmetric tensors, Sec. II B).  q_ptrs has L+1 entries;
+ * q_ptrs[k] is a host array of chi_k ints (chi from tebd_bond_dims): for each
+ * Schmidt index of bond k, the number of bosons on the sites left of the bond.
+ * Each array must be non-decreasing (every charge one contiguous run of the
+ * index), 0 <= q <= n_max k, and q_ptrs[0][0] = 0.  The installed state must
+ * vanish outside its blocks, B_k[a, s, b] = 0 unless q_{k+1}[b] = q_k[a] + s:
+ * the blocked update reads only those blocks.  tebd_init_product sets the
+ * charges of its product state itself; tebd_set_state clears them, and a
+ * blocked step without them returns TEBD_ERR_STATE.  Arrays are read before
+ * the call returns. */
+int tebd_set_charges(tebd_handle h, const int* const* q_ptrs);
+
+/* Copy the charges of bond k (0 <= k <= L) into q[chi_k] (host).  After every
+ * blocked local update the new bonds are sorted by charge.  TEBD_ERR_STATE if
+ * the handle has no charges (after tebd_set_state without tebd_set_charges). */
+int tebd_get_charges(tebd_handle h, int k, int* q);
 
 /* Number of local updates (three-site gates) applied since init, and the
  * number of CUDA kernels this handle has launched since create.

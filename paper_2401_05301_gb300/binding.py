@@ -36,6 +36,8 @@ SIGNATURES = {
     "tebd_bond_dims": (_c_int, [_c_void_p, _P_int]),
     "tebd_get_site": (_c_int, [_c_void_p, _c_int, _P_double, _P_double]),
     "tebd_set_state": (_c_int, [_c_void_p, _P_int, ctypes.POINTER(_P_double), ctypes.POINTER(_P_double)]),
+    "tebd_set_charges": (_c_int, [_c_void_p, ctypes.POINTER(_P_int)]),
+    "tebd_get_charges": (_c_int, [_c_void_p, _c_int, _P_int]),
     "tebd_counters": (_c_int, [_c_void_p, _P_ll, _P_ll]),
     "tebd_profile": (_c_int, [_c_void_p, _c_int, _P_double, _P_ll, _P_double]),
     "tebd_destroy": (None, [_c_void_p]),
@@ -119,7 +121,7 @@ class TEBD:
     """One simulation handle (see include/ptebd.h for every call's contract)."""
 
     def __init__(self, L, n_max, chi_max, U, J, Jnnn, K, jc, dt, w_cut=None, eps_rel=None, precision=None,
-                 stream=None):
+                 stream=None, u1=None):
         lib = load()
         h = _c_void_p()
         _check(lib.tebd_create(L, n_max, chi_max, U, J, Jnnn, K, jc, dt, ctypes.byref(h)), "tebd_create")
@@ -131,6 +133,8 @@ class TEBD:
             self.set_option("eps_rel", eps_rel)
         if precision is not None:
             self.set_option("precision", precision)
+        if u1 is not None:
+            self.set_option("u1", 1 if u1 else 0)
         if stream is not None:
             self.set_stream(stream)
 
@@ -187,6 +191,19 @@ class TEBD:
         Bp = (_P_double * len(Bs))(*[_dptr(b) for b in Bs])
         lp = (_P_double * len(ls))(*[_dptr(x) for x in ls])
         _check(load().tebd_set_state(self._h, chi.ctypes.data_as(_P_int), Bp, lp), "tebd_set_state")
+
+    def set_charges(self, q):
+        """Bond charge labels for the particle-number-blocked form (tebd_set_charges): q[k] holds, per
+        Schmidt index of bond k, the boson count left of the bond, non-decreasing."""
+        qs = [np.ascontiguousarray(x, dtype=np.int32) for x in q]
+        qp = (_P_int * len(qs))(*[x.ctypes.data_as(_P_int) for x in qs])
+        _check(load().tebd_set_charges(self._h, qp), "tebd_set_charges")
+
+    def get_charges(self, k: int):
+        chi = self.bond_dims()
+        out = np.empty(chi[k], dtype=np.int32)
+        _check(load().tebd_get_charges(self._h, k, out.ctypes.data_as(_P_int)), "tebd_get_charges")
+        return out
 
     def counters(self):
         g, k = ctypes.c_longlong(), ctypes.c_longlong()

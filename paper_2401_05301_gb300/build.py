@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libptebd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["api.cu", "kernels_gemm.cu", "kernels_eig.cu", "kernels_misc.cu", "kernels_tf32.cu", "kernels_ozaki.cu",
-           "noalloc.cu",
+           "noalloc.cu", "u1.cu",
            "gates_host.cpp"]
 
 

@@ -1,8 +1,7 @@
 // C ABI of the three-site TEBD library: handle, device state, and the host
 // orchestration of one Trotter layer (all triples with the same start mod 3
 // processed as one batch of independent local updates).
-#include "ptebd.h"
-#include "ptebd_internal.h"
+#include "ptebd_ctx.h"
 
 #include <algorithm>
 #include <cmath>
@@ -16,86 +15,11 @@
 
 using namespace ptebd;
 
-struct tebd_ctx;
-
 namespace {
-
-constexpr int MAX_SLOTS = 24;
 constexpr int MEAS_CHUNK = GEMM_MAXP;
-
-struct Slot {
-  double2 *X, *Th, *Cb, *H, *V1h, *tau, *part, *p, *U;
-  double *d, *e, *evals, *Z, *Z2, *S, *work, *s_sorted, *scal;  // scal: [0] trace [1] norm [2] w
-  int *perm, *chi;
-  double2* pan;  // panel arrays of the blocked tridiagonal reduction
-  void* oz;  // digit planes of the mixed path's Gram and projection products (null in FP64)
-};
-
-struct Triple {
-  tebd_ctx* h;  // the simulation this triple belongs to
-  int i;        // 0-based first site
-  int slot;
-  int chl, c1, c2, chr;
-  int m1, n1, K1, chi1, m2, n2, K2, chi2;
-  double norm1, norm2, w1, w2;
-};
-
 }  // namespace
 
-struct tebd_ctx {
-  int L = 0, n_max = 0, d = 0, D = 0, chi_max = 0;
-  double U = 0, J = 0, Jnnn = 0, K = 0, jc = 0, dt = 0;
-  double w_cut = 0.0, eps_rel = 1e-12;
-  int precision = 0, max_slots = 0;
-  int order = 2;  // Trotter order: 2 or 4 (gate table and layer schedule follow it)
-  int jacobi_sweeps = 60;  // sweep limit of the host gate builder's Jacobi eigen-solver
-  long long wait_clocks = 2000000000LL;  // limit of each grid-barrier wait in the reduction (~1 s)
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int sticky = TEBD_OK;
-  bool have_state = false;
-  std::vector<int> cap, chi;
-  std::vector<double2*> B;
-  std::vector<double*> lam;
-  double2* G = nullptr;
-  double2** dB = nullptr;
-  double** dlam = nullptr;
-  int* d_status = nullptr;
-  int* d_occ = nullptr;
-  unsigned int* d_bar = nullptr;  // grid-barrier state of the persistent reduction
-  std::vector<Slot> slots;
-  long long capmax = 0, mmax = 0, n1max = 0, kcap = 0;
-  double* h_pinned = nullptr;
-  size_t h_pinned_n = 0;
-  double2 *mP = nullptr, *mQ = nullptr, *mX = nullptr, *mY = nullptr, *mC = nullptr;
-  double* mN = nullptr;
-  double w_total = 0.0;
-  long long steps = 0, gate_updates = 0, launches = 0;
-  std::vector<void*> allocs;
-  // optional per-class timing (CUDA events on the handle's stream)
-  bool prof = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[TEBD_PROF_NCLASS];
-  std::vector<int> prof_pending_cls;
-  double prof_ms[TEBD_PROF_NCLASS] = {};
-  long long prof_launches[TEBD_PROF_NCLASS] = {};
-  double prof_work[TEBD_PROF_NCLASS] = {};
-  std::vector<cudaEvent_t> event_pool;
-};
-
-namespace {
-
-bool is_fin(double x) { return std::isfinite(x); }
-
-cudaEvent_t get_event(tebd_ctx* c) {
-  if (!c->event_pool.empty()) {
-    cudaEvent_t e = c->event_pool.back();
-    c->event_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e;
-  cudaEventCreate(&e);
-  return e;
-}
+namespace ptebd {
 
 // Fold every finished event pair into the per-class totals (call after a sync).
 void prof_collect(tebd_ctx* c) {
@@ -111,39 +35,6 @@ void prof_collect(tebd_ctx* c) {
   cudaGetLastError();
 }
 
-// Times the launches issued during its lifetime as one interval of class cls.
-struct ProfScope {
-  tebd_ctx* c;
-  int cls;
-  long long l0;
-  cudaEvent_t a = nullptr;
-  ProfScope(tebd_ctx* c_, int cls_, double work) : c(c_), cls(cls_), l0(c_->launches) {
-    if (!c->prof) return;
-    c->prof_work[cls] += work;
-    a = get_event(c);
-    cudaEventRecord(a, c->stream);
-  }
-  ~ProfScope() {
-    if (!c->prof) return;
-    cudaEvent_t b = get_event(c);
-    cudaEventRecord(b, c->stream);
-    c->prof_pending[cls].push_back({a, b});
-    c->prof_launches[cls] += c->launches - l0;
-  }
-};
-
-template <typename T>
-T* dalloc(tebd_ctx* c, size_t count) {
-  void* p = nullptr;
-  if (count == 0) count = 1;
-  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  c->allocs.push_back(p);
-  return static_cast<T*>(p);
-}
-
 int fail_cuda(tebd_ctx* c) {
   c->sticky = TEBD_ERR_CUDA;
   return TEBD_ERR_CUDA;
@@ -157,8 +48,6 @@ int check_launch(tebd_ctx* c) {
   }
   return TEBD_OK;
 }
-
-void prof_collect(tebd_ctx* c);
 
 int sync(tebd_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -191,6 +80,10 @@ int ensure_pinned(tebd_ctx* c, size_t n) {
   c->h_pinned_n = n;
   return TEBD_OK;
 }
+
+}  // namespace ptebd
+
+namespace {
 
 int max_triples_per_layer(int L) {
   int best = 0;
@@ -276,6 +169,7 @@ int build_gates(tebd_ctx* c) {
     cudaGetLastError();
     return TEBD_ERR_CUDA;
   }
+  if (int r = u1_build_gate_blocks(c, Gall, taus.size() * L2)) return r;
   if (c->G) {  // replace the previous table
     for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
       if (*it == c->G) { c->allocs.erase(it); break; }
@@ -287,6 +181,13 @@ int build_gates(tebd_ctx* c) {
 
 int alloc_workspace(tebd_ctx* c) {
   if (!c->slots.empty()) return TEBD_OK;
+  if (c->u1) {  // the blocked form: slots hold only arenas that grow with the blocks
+    int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
+    if (c->max_slots > 0) want = std::min(want, c->max_slots);
+    if (int r = u1_alloc_slots(c, want)) return r;
+    c->slots.assign(want, Slot{});
+    return ensure_pinned(c, 64);
+  }
   const long long d = c->d;
   long long capmax = 1;
   for (int v : c->cap) capmax = std::max<long long>(capmax, v);
@@ -885,7 +786,7 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
       ts.push_back(T);
       if (k) ++*k; else used.push_back({p.h, 1});
     }
-    if (int r = update_chunk(c, ts, tidx)) return r;
+    if (int r = c->u1 ? update_chunk_u1(c, ts, tidx) : update_chunk(c, ts, tidx)) return r;
     rest.swap(later);
   }
   return TEBD_OK;
@@ -1095,6 +996,12 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
       h->prof_launches[q] = 0;
       h->prof_work[q] = 0.0;
     }
+  } else if (k == "u1") {
+    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if ((value == 1.0) != h->u1) {
+      if (!h->slots.empty()) return TEBD_ERR_STATE;  // the workspace is laid out for one form
+      h->u1 = (value == 1.0);
+    }
   } else if (k == "jacobi_max_sweeps") {
     if (value < 1 || value > 1000 || value != std::floor(value)) return TEBD_ERR_ARG;
     if ((int)value != h->jacobi_sweeps) {
@@ -1135,10 +1042,41 @@ int tebd_init_product(tebd_handle h, const int* occ) {
   if (int r = check_launch(h)) return r;
   if (int r = sync(h)) return r;  // occ is pageable caller memory
   std::fill(h->chi.begin(), h->chi.end(), 1);
+  // bond charges of a product state: the boson count left of each bond
+  h->q.assign(h->L + 1, std::vector<int>(1, 0));
+  for (int k = 1; k <= h->L; ++k) h->q[k][0] = h->q[k - 1][0] + occ[k - 1];
+  h->have_charges = true;
   h->steps = 0;
   h->w_total = 0.0;
   h->gate_updates = 0;
   h->have_state = true;
+  return TEBD_OK;
+}
+
+int tebd_set_charges(tebd_handle h, const int* const* q_ptrs) {
+  CHECK_HANDLE(h);
+  if (!q_ptrs) return TEBD_ERR_ARG;
+  if (!h->have_state) return TEBD_ERR_STATE;
+  std::vector<std::vector<int>> q(h->L + 1);
+  for (int k = 0; k <= h->L; ++k) {
+    if (!q_ptrs[k]) return TEBD_ERR_ARG;
+    q[k].assign(q_ptrs[k], q_ptrs[k] + h->chi[k]);
+    for (int a = 0; a < h->chi[k]; ++a) {
+      if (q[k][a] < 0 || q[k][a] > h->n_max * k) return TEBD_ERR_ARG;
+      if (a > 0 && q[k][a] < q[k][a - 1]) return TEBD_ERR_ARG;  // each charge one contiguous run
+    }
+  }
+  if (q[0][0] != 0) return TEBD_ERR_ARG;
+  h->q.swap(q);
+  h->have_charges = true;
+  return TEBD_OK;
+}
+
+int tebd_get_charges(tebd_handle h, int k, int* q) {
+  CHECK_HANDLE(h);
+  if (!q || k < 0 || k > h->L) return TEBD_ERR_ARG;
+  if (!h->have_charges) return TEBD_ERR_STATE;
+  std::copy(h->q[k].begin(), h->q[k].end(), q);
   return TEBD_OK;
 }
 
@@ -1159,6 +1097,7 @@ int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs, c
       return fail_cuda(h);
   }
   h->chi.assign(chi, chi + h->L + 1);
+  h->have_charges = false;  // tebd_set_charges supplies them for the blocked form
   h->steps = 0;
   h->w_total = 0.0;
   h->gate_updates = 0;
@@ -1169,7 +1108,7 @@ int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs, c
 int tebd_step(tebd_handle h, int n_steps) {
   CHECK_HANDLE(h);
   if (n_steps < 0) return TEBD_ERR_ARG;
-  if (!h->have_state) return TEBD_ERR_STATE;
+  if (!h->have_state || (h->u1 && !h->have_charges)) return TEBD_ERR_STATE;
   if (n_steps == 0) return TEBD_OK;
   try {
     if (int r = alloc_workspace(h)) return r;
@@ -1213,8 +1152,10 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
     if (!hs[i]) return TEBD_ERR_ARG;
     if (hs[i]->sticky != TEBD_OK) return hs[i]->sticky;
     if (!hs[i]->have_state) return TEBD_ERR_STATE;
-    if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision || hs[i]->order != hs[0]->order)
+    if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision || hs[i]->order != hs[0]->order ||
+        hs[i]->u1 != hs[0]->u1)
       return TEBD_ERR_ARG;
+    if (hs[i]->u1 && !hs[i]->have_charges) return TEBD_ERR_STATE;
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return TEBD_ERR_ARG;
   }
@@ -1244,7 +1185,7 @@ int tebd_layer(tebd_handle h, int residue, int full) {
   CHECK_HANDLE(h);
   if (residue < 0 || residue > 2 || (full != 0 && full != 1)) return TEBD_ERR_ARG;
   if (h->order != 2) return TEBD_ERR_ARG;  // the gate table holds dt/2 and dt only at order 2
-  if (!h->have_state) return TEBD_ERR_STATE;
+  if (!h->have_state || (h->u1 && !h->have_charges)) return TEBD_ERR_STATE;
   try {
     if (int r = alloc_workspace(h)) return r;
     return run_layer(h, residue, full);
@@ -1355,6 +1296,8 @@ void tebd_destroy(tebd_handle h) {
   else cudaDeviceSynchronize();
   prof_collect(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  u1_release(h);
+  if (h->Gblk) cudaFree(h->Gblk);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   cudaGetLastError();

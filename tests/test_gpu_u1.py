@@ -1,0 +1,245 @@
+"""GPU particle-number-blocked form (option "u1", the paper's U(1)-symmetric
+decompositions of Sec. II B) against the CPU oracles, on the same seeded inputs.
+
+The blocked form keeps each bond sorted by charge and takes every SVD block by
+block, so its Schmidt vectors are a gauge transform of the dense ones:
+observables, sorted spectra, charge multisets and truncation decisions are
+compared, never raw tensors.  Bounds: 1e-9 on densities and currents for the
+FP64 (precision 0) and exact-digit (precision 2) paths, 1e-5 for the mixed
+path (precision 1), 1e-10 on the kept spectra.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle.tebd import TEBD as OracleTEBD
+from oracle.u1 import U1TEBD
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+TOL_MIXED = 1e-5
+
+
+def _args(wl, **kw):
+    a = dict(L=wl.L, n_max=wl.n_max, chi_max=wl.chi_max, U=wl.U, J=wl.J, Jnnn=wl.Jnnn, K=wl.K, jc=wl.jc,
+             dt=wl.dt, w_cut=wl.w_cut, eps_rel=wl.eps_rel)
+    a.update(kw)
+    return a
+
+
+def _gpu(wl, precision=0, **kw):
+    from paper_2401_05301_gb300 import TEBD
+    return TEBD(**_args(wl, **kw), precision=precision, u1=True)
+
+
+def _check_bonds(g, o, spectra_tol=1e-10):
+    """Same chi' on every bond, the same charge multiset and (where chi' agrees) the same
+    sorted spectrum; every bond of the GPU state sorted by charge."""
+    chi_g, chi_o = list(g.bond_dims()), o.chi()
+    differ = [k for k, (a, b) in enumerate(zip(chi_g, chi_o)) if a != b]
+    for k in range(g.L + 1):
+        qg = g.get_charges(k)
+        assert np.all(np.diff(qg) >= 0), f"bond {k} not sorted by charge"
+        if k in differ:
+            continue
+        assert np.array_equal(np.sort(qg), np.sort(o.q[k])), f"bond {k} charges"
+        lg = np.sort(g.get_lambda(k))[::-1]
+        lo = np.sort(o.lam[k])[::-1]
+        assert np.max(np.abs(lg - lo)) < spectra_tol, (k, np.max(np.abs(lg - lo)))
+    return differ
+
+
+def _compare_run(wl, n_steps, every, precision=0, tol=TOL, bonds=True, **kw):
+    g = _gpu(wl, precision, **kw)
+    o = U1TEBD(**_args(wl, **kw))
+    occ = wl.occupation()
+    g.init_product(occ)
+    o.init_product(occ)
+    worst = 0.0
+    for k in range(every, n_steps + 1, every):
+        g.step(every)
+        o.step(every)
+        n_g, cur_g = g.measure()
+        err = max(np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+        differ = _check_bonds(g, o) if bonds else []
+        assert err < tol, (f"step {k}: max |dn|,|dcur| = {err:.3e}; chi' differs on bonds {differ}; smallest "
+                           f"relative gap at a cut {o.min_cut_gap:.2e}" + ("  -> unpinned at a truncation tie"
+                                                                           if differ else ""))
+        assert not differ or o.min_cut_gap < 1e-6, f"chi' differs on bonds {differ} without a near tie"
+        worst = max(worst, err)
+    t, w, _ = g.stats()
+    assert abs(t - n_steps * wl.dt) < 1e-12
+    assert abs(w - o.w_total) <= 1e-9 * max(1.0, o.w_total) + 1e-14
+    g.close()
+    return worst
+
+
+def test_u1_product_state_charges(lib):
+    wl = workloads.PARITY_L8
+    g = _gpu(wl)
+    occ = wl.occupation()
+    g.init_product(occ)
+    for k in range(wl.L + 1):
+        assert list(g.get_charges(k)) == [int(np.sum(occ[:k]))]
+    g.close()
+
+
+def test_u1_small_chain_matches_oracle(lib):
+    wl = workloads.Workload("small", L=6, n_max=2, chi_max=64, U=2.0, J=1.0, Jnnn=0.2, K=0.05, jc=3.5,
+                            dt=0.05, t_end=1.0)
+    worst = _compare_run(wl, 20, 5)
+    print(f"u1 small chain: max |delta| = {worst:.3e}")
+
+
+def test_u1_parity_L8_trajectory(lib):
+    """L=8, d=4, N=4, chi_max=256 (untruncated up to the paper's eps), t = 0..2 every 0.2."""
+    wl = workloads.PARITY_L8
+    worst = _compare_run(wl, 200, 20)
+    print(f"u1 L8 parity: max |delta| = {worst:.3e}")
+
+
+def test_u1_L8_matches_dense_oracle(lib):
+    """The blocked form against the dense oracle (a different decomposition route)."""
+    wl = workloads.PARITY_L8
+    g = _gpu(wl)
+    o = OracleTEBD(**_args(wl))
+    g.init_product(wl.occupation())
+    o.init_product(wl.occupation())
+    g.step(100)
+    o.step(100)
+    n_g, cur_g = g.measure()
+    err = max(np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+    g.close()
+    print(f"u1 vs dense oracle, L8 t=1: {err:.3e}")
+    assert err < TOL
+
+
+def test_u1_parity_L32_truncating(lib):
+    """L=32, d=4, w_cut = 1e-10, to t = 0.6."""
+    worst = _compare_run(workloads.TRUNC_L32, 60, 20)
+    print(f"u1 L32 parity: max |delta| = {worst:.3e}")
+
+
+def test_u1_exact_digit_path(lib):
+    worst = _compare_run(workloads.PARITY_L8, 100, 20, precision=2)
+    print(f"u1 exact-digit parity: max |delta| = {worst:.3e}")
+
+
+def test_u1_mixed_path(lib):
+    """precision 1: 3xTF32 contractions; the decompositions FP64-accurate.  Spectra are
+    not compared (the contractions move them by ~1e-6); chi' and observables are."""
+    wl = workloads.PARITY_L8
+    g = _gpu(wl, 1)
+    o = U1TEBD(**_args(wl))
+    g.init_product(wl.occupation())
+    o.init_product(wl.occupation())
+    worst = 0.0
+    for _ in range(5):
+        g.step(20)
+        o.step(20)
+        n_g, cur_g = g.measure()
+        worst = max(worst, np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+    g.close()
+    print(f"u1 mixed path, L8 t=1: max |dn|,|dcur| = {worst:.3e} (bound {TOL_MIXED:g})")
+    assert worst < TOL_MIXED
+
+
+def test_u1_fourth_order(lib):
+    wl = workloads.PARITY_L8
+    g = _gpu(wl)
+    g.set_option("trotter_order", 4)
+    o = U1TEBD(**_args(wl), order=4)
+    g.init_product(wl.occupation())
+    o.init_product(wl.occupation())
+    g.step(30)
+    o.step(30)
+    n_g, cur_g = g.measure()
+    err = max(np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+    g.close()
+    assert err < TOL
+
+
+@pytest.mark.parametrize("L,n_max,chi", [(3, 3, 64), (4, 1, 4), (5, 2, 1), (7, 2, 3), (9, 3, 5)])
+def test_u1_edge_shapes(lib, L, n_max, chi):
+    wl = workloads.Workload("edge", L=L, n_max=n_max, chi_max=chi, U=1.5, J=1.0, Jnnn=0.3, K=0.02,
+                            jc=(L + 1) / 2, dt=0.05, t_end=0.5, w_cut=1e-8)
+    _compare_run(wl, 10, 5)
+
+
+def test_u1_paper_setup_flanked_cdw(lib):
+    """L = 121, d = 5, flanked CDW of 27 bosons, Table Ib set a, chi_max = 40, eight steps."""
+    worst = _compare_run(workloads.paper_run("a", 27, 40), 8, 2, bonds=False)
+    print(f"u1 paper setup parity: max |delta| = {worst:.3e}")
+
+
+def test_u1_synthetic_state_layer(lib):
+    """A charge-labelled saturated state (L=12, d=4, chi=64, N=6): one layer of each kind
+    through tebd_layer against the oracle's same layer."""
+    from paper_2401_05301_gb300 import TEBD
+    L, n_max, chi, N = 12, 3, 64, 6
+    wl = workloads.Workload("syn", L=L, n_max=n_max, chi_max=chi, U=4.0, J=1.0, Jnnn=0.1, K=0.01,
+                            jc=(L + 1) / 2, dt=0.01, t_end=0.1, w_cut=1e-12)
+    B, lam, q = workloads.synthetic_state_u1(L, n_max + 1, chi, N)
+    g = TEBD(**_args(wl), u1=True)
+    g.set_state(B, lam)
+    g.set_charges(q)
+    o = U1TEBD(**_args(wl))
+    o.set_state(B, lam, q)
+    for residue, full in ((0, False), (1, False), (2, True)):
+        g.layer(residue, full)
+        tau = wl.dt if full else wl.dt / 2
+        for j in range(residue + 1, L - 1, 3):
+            o.apply_gate(j - 1, o.gate(j, tau))
+        n_g, cur_g = g.measure()
+        err = max(np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
+        assert err < TOL, (residue, err)
+        assert not _check_bonds(g, o)
+    assert abs(np.sum(n_g) - N) < 1e-10
+    g.close()
+
+
+def test_u1_charges_validation(lib):
+    from paper_2401_05301_gb300 import TEBD, TEBDError
+    L, n_max, chi, N = 8, 2, 16, 4
+    B, lam, q = workloads.synthetic_state_u1(L, n_max + 1, chi, N)
+    g = TEBD(L, n_max, chi, 2.0, 1.0, 0.1, 0.0, 4.5, 0.01, u1=True)
+    g.set_state(B, lam)
+    with pytest.raises(TEBDError) as e:
+        g.step(1)  # no charges after set_state
+    assert e.value.status == -4
+    bad = [x.copy() for x in q]
+    k = next(i for i, x in enumerate(bad) if len(np.unique(x)) > 1)
+    bad[k] = bad[k][::-1].copy()  # not sorted
+    with pytest.raises(TEBDError):
+        g.set_charges(bad)
+    g.set_charges(q)
+    g.step(1)
+    with pytest.raises(TEBDError):
+        g.set_option("u1", 0)  # the workspace is laid out for the blocked form
+    g.close()
+
+
+def test_u1_batch_is_bitwise_the_same_as_alone(lib):
+    from paper_2401_05301_gb300 import TEBD, batch_step
+    sims = [(9, 2, 32, 2.0, 1.0, 0.1, 0.01, 5.0, 0.02, 1e-10), (12, 3, 64, 5.0, 1.0, 0.12, 0.005, 6.5, 0.01, 0.0),
+            (7, 4, 128, 3.0, 1.0, 0.05, 0.0, 4.0, 0.01, 0.0)]
+
+    def make(p):
+        L, n_max, chi, U, J, Jnnn, K, jc, dt, wc = p
+        g = TEBD(L, n_max, chi, U, J, Jnnn, K, jc, dt, w_cut=wc, u1=True)
+        g.init_product(workloads.cdw(L))
+        return g
+
+    alone = []
+    for p in sims:
+        g = make(p)
+        g.step(12)
+        alone.append(np.concatenate(g.measure()))
+        g.close()
+    hs = [make(p) for p in sims]
+    for _ in range(3):
+        batch_step(hs, 4)
+    for g, ref in zip(hs, alone):
+        assert np.array_equal(np.concatenate(g.measure()), ref)
+        g.close()
