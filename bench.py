@@ -1,18 +1,27 @@
 """Benchmark: TEBD gate-updates/s at chi_max on one GB300 (and N replicas).
 
-Workload (default): L=32 Bose-Hubbard chain with NN+NNN hopping and a trap
-(U=5, J=1, J_NNN=0.12, K=0.005, j_c=16.5), d=4, chi_max=256, discarded-weight
-cut 1e-10, dt=0.01, started from the seeded synthetic saturated state
-(chi = min(256, 4^min(k, 32-k)) on every bond).  One step = one full
-second-order Trotter step (A/2 B/2 C B/2 A/2 = 50 three-site gate updates,
-100 truncated SVDs) plus the density/current measurement.  The state and
-the workspace (> 2 GB) exceed L2 (129 MB), so no flush is needed between steps.
+Workload (default, "config3_u1"): the mixed-precision chain of L = 64 sites,
+n_max = 4 (d = 5), U = 3, J = 1, J_NNN = 0.1, K = 0.003 about j_c = 32.5,
+dt = 0.005, chi_max = 1024, relative cut eps = 1e-12, at half filling
+(N = 32), started from the seeded charge-labelled synthetic saturated state
+(chi_k = min(1024, 5^min(k, 64-k)): bonds 5..59 at chi_max = 1024; right-
+canonical charge blocks; lambda with p_i ~ exp(-8 i / chi)).  One step = one
+full second-order Trotter step (A/2 B/2 C B/2 A/2 = 104 three-site gate
+updates, 208 truncated SVDs) plus the density/current measurement, on the
+particle-number-blocked form of the update (the paper's U(1)-symmetric
+decompositions, Sec. II B).  The state (5.4 GB) and workspace exceed L2
+(129 MB), so no flush is needed between steps.
+
+value: the mixed path (3xTF32 tensor-core contractions, FP64-accurate
+decompositions).  Beside it: the plain FP64 path and the FP64-accurate
+exact-digit path on the same state (a stated number of steps each), and the
+dense form on the L = 32, d = 4, chi = 256 chain.
 
 Multi-GPU: replicas only (independent simulations, one per rank, no
 collective on the data path); value = all ranks' gate updates / max time.
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (a few gate updates per step).
+--impl reference times the CPU oracle on the host cores on a bounded sample
+of the same workload (see run_reference).
 """
 from __future__ import annotations
 
@@ -33,24 +42,25 @@ if ROOT not in sys.path:
 
 import workloads  # noqa: E402
 
-WL = workloads.TRUNC_L32
-WORKLOADS = {"trunc_L32": workloads.TRUNC_L32, "parity_L8": workloads.PARITY_L8,
-             "sample_L16_d5_chi1024": workloads.SAMPLE_L16_D5}
+HEAD = workloads.MIXED_L64
+N_HEAD = 32              # bosons of the 64-site half-filled CDW
+SIDE_STEPS = 3           # timed steps of the FP64 and exact-digit side arms
+REF_CHI = 384           # chi_max of the reference arm's CPU sample (see run_reference)
 
-
-def gates_per_step(L: int) -> int:
-    """Three-site gate updates in one A/2 B/2 C B/2 A/2 step (50 for L = 32)."""
-    n = {r: len(range(r, L - 2, 3)) for r in range(3)}
-    return 2 * n[0] + 2 * n[1] + n[2]
-
-
-METRIC = "TEBD gate-updates/s at \u03c7_max, mixed vs FP64 on 1 GB300; served p50/p99 latency"
+METRIC = "TEBD gate-updates/s at χ_max, mixed vs FP64 on 1 GB300; served p50/p99 latency"
 UNIT = "gate-updates/s"
 # FP64 on GB300: 152 SMs x 2 DFMA (4 flop) per clock x 2070 MHz (a DFMA throughput
 # probe measured 1.20 TFLOP/s at ~1970 MHz, i.e. 2 DFMA/clk/SM).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 # TF32 dense: measured bf16 peak x nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s).
 TF32_RATIO = 1.1 / 2.25
+ALU_CLASSES = ("tridiag", "bisect", "eigvec")
+
+
+def gates_per_step(L: int) -> int:
+    """Three-site gate updates in one A/2 B/2 C B/2 A/2 step (104 for L = 64, 50 for L = 32)."""
+    n = {r: len(range(r, L - 2, 3)) for r in range(3)}
+    return 2 * n[0] + 2 * n[1] + n[2]
 
 
 def measured_peaks():
@@ -61,11 +71,23 @@ def measured_peaks():
         return {}
 
 
-def config(precision: str):
-    return {"workload": f"L{WL.L}_d{WL.d}_chi{WL.chi_max}_wcut{WL.w_cut:g}_synthetic_saturated",
-            "L": WL.L, "d": WL.d, "chi_max": WL.chi_max, "dt": WL.dt, "precision": precision,
-            "step": f"one 2nd-order Trotter step ({gates_per_step(WL.L)} three-site gate updates) + n_j/current measurement",
-            "l2_flush": "not needed: state + workspace > 2 GB > 129 MB L2"}
+def blas_vendor() -> str:
+    try:
+        b = np.__config__.CONFIG["Build Dependencies"]["blas"]
+        return f"{b.get('name')} {b.get('version')}"
+    except Exception:  # noqa: BLE001 - a description only
+        return "unknown"
+
+
+def head_config(precision: str):
+    wl = HEAD
+    return {"workload": f"L{wl.L}_d{wl.d}_chi{wl.chi_max}_N{N_HEAD}_u1_synthetic_saturated",
+            "L": wl.L, "d": wl.d, "chi_max": wl.chi_max, "N": N_HEAD, "U": wl.U, "J": wl.J, "J_NNN": wl.Jnnn,
+            "K": wl.K, "j_c": wl.jc, "dt": wl.dt, "eps_rel": wl.eps_rel, "w_cut": wl.w_cut, "precision": precision,
+            "form": "particle-number (U(1)) blocked local update, dense site tensors in HBM",
+            "step": f"one 2nd-order Trotter step ({gates_per_step(wl.L)} three-site gate updates) + n_j/current "
+                    "measurement",
+            "l2_flush": "not needed: state (5.4 GB) + workspace > 129 MB L2"}
 
 
 class ClockSampler:
@@ -133,11 +155,11 @@ def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
-def side_measurement(fn, *args):
+def side_measurement(fn, *args, **kw):
     """Run a measurement reported beside the headline; if it fails, record why instead of losing the line."""
     try:
-        return fn(*args)
-    except Exception as e:
+        return fn(*args, **kw)
+    except Exception as e:  # noqa: BLE001 - reported, not swallowed
         return {"error": f"{type(e).__name__}: {e}"}
 
 
@@ -146,20 +168,103 @@ def job_value(updates_per_rank: int, ws: int, seconds_max: float) -> float:
     return updates_per_rank * ws / seconds_max
 
 
-def oracle_sample(n_gates: int, seed_state):
-    """Time the oracle on n_gates three-site updates of the saturated state (layer A order)."""
-    from oracle.tebd import TEBD as OracleTEBD
-    B, lam, _ = seed_state
-    o = OracleTEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
-                   eps_rel=WL.eps_rel)
-    o.set_state(B, lam)
-    triples = [j for j in range(1, WL.L - 1) if j % 3 == 1]
-    gates = [o.gate(j, WL.dt / 2) for j in triples]  # built before timing (host setup, not the path)
-    t0 = time.perf_counter()
-    for q in range(n_gates):
-        k = (q + 3) % len(triples)  # interior triples first
-        o.apply_gate(triples[k] - 1, gates[k])
-    return time.perf_counter() - t0
+def head_state(seed: int = workloads.SEED, chi_max: int = HEAD.chi_max):
+    return workloads.synthetic_state_u1(HEAD.L, HEAD.d, chi_max, N_HEAD, seed=seed)
+
+
+def oracle_update_seconds(state, chi_max: int = HEAD.chi_max, n: int = 1) -> float:
+    """Time the U(1) oracle on n gate updates of the interior triple on sites 31..33 of the
+    charge-labelled saturated chain (the gate is built before the clock starts)."""
+    from oracle.u1 import U1TEBD
+    B, lam, q = state
+    o = U1TEBD(HEAD.L, HEAD.n_max, chi_max, HEAD.U, HEAD.J, HEAD.Jnnn, HEAD.K, HEAD.jc, HEAD.dt,
+               w_cut=HEAD.w_cut, eps_rel=HEAD.eps_rel)
+    total = 0.0
+    G = o.gate(31, HEAD.dt / 2)
+    for _ in range(n):
+        o.set_state(B, lam, q)
+        t0 = time.perf_counter()
+        o.apply_gate(30, G)
+        total += time.perf_counter() - t0
+    return total
+
+
+def profile_summary(prof):
+    return {"classes_ms": {k: round(v[0], 3) for k, v in prof.items()},
+            "classes_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] > 0 and v[2] > 0 else None)
+                               for k, v in prof.items()}}
+
+
+def make_head(precision: int, stream_ptr: int, state):
+    from paper_2401_05301_gb300 import TEBD
+    wl = HEAD
+    g = TEBD(wl.L, wl.n_max, wl.chi_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, wl.dt, w_cut=wl.w_cut,
+             eps_rel=wl.eps_rel, precision=precision, stream=stream_ptr, u1=True)
+    B, lam, q = state
+    g.set_state(B, lam)
+    g.set_charges(q)
+    return g
+
+
+def time_path(precision: int, state, stream, steps: int, warmup: int, ws: int, barrier):
+    """A side arm on the headline state: warmup + steps full steps, device-timed."""
+    import torch
+    g = make_head(precision, stream.cuda_stream, state)
+    for _ in range(warmup):
+        g.step(1)
+        g.measure()
+    g.set_option("profile", 1)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(steps):
+        g.step(1)
+        g.measure()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fms = max_over_ranks(f0.elapsed_time(f1), ws)
+    pp = g.profile()
+    g.close()
+    out = {"value": job_value(gates_per_step(HEAD.L) * steps, ws, fms / 1e3), "unit": UNIT,
+           "steps": steps, "warmup": warmup, "ms_per_step": fms / steps}
+    out.update(profile_summary(pp))
+    return out
+
+
+def dense_config2(stream, steps: int = 2, warmup: int = 1):
+    """The dense form on the L = 32, d = 4, chi = 256 chain (w_cut = 1e-10) from its seeded
+    synthetic saturated state: mixed, plain FP64 and exact-digit paths."""
+    import torch
+    from paper_2401_05301_gb300 import TEBD
+    wl = workloads.TRUNC_L32
+    B, lam, _ = workloads.synthetic_state(wl.L, wl.d, wl.chi_max)
+    out = {"workload": f"L{wl.L}_d{wl.d}_chi{wl.chi_max}_wcut{wl.w_cut:g}_synthetic_saturated (dense form)",
+           "steps": steps, "warmup": warmup}
+    for name, prec in (("mixed", 1), ("fp64", 0), ("exact", 2)):
+        g = TEBD(wl.L, wl.n_max, wl.chi_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, wl.dt, w_cut=wl.w_cut,
+                 eps_rel=wl.eps_rel, precision=prec, stream=stream.cuda_stream)
+        g.set_state(B, lam)
+        for _ in range(warmup):
+            g.step(1)
+        g.set_option("profile", 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.step(1)
+            g.measure()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = g.profile()
+        g.close()
+        tri = prof["tridiag"]
+        out[name] = {"value": gates_per_step(wl.L) * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "tridiag_frac_of_fp64_peak": (tri[2] / (tri[0] / 1e3) / 1e12 / FP64_PEAK_TFLOPS
+                                                   if tri[0] > 0 else None)}
+        out[name].update(profile_summary(prof))
+    return out
 
 
 def served_requests(n: int = 24, rate: float = 8.0):
@@ -240,25 +345,43 @@ def batched_measurement(stream_ptr, steps: int = 10):
 
 
 def run_reference(args):
+    """The CPU oracle (oracle/u1.py, numpy + LAPACK FP64, the machine's host cores) on the headline
+    chain's physics.  One oracle update of a saturated triple at chi_max = 1024 takes ~50 s on 8
+    x86 host cores (measured), so no bounded run of --steps K full-size updates fits in minutes;
+    each step here is one update of the same interior triple of the same charge-labelled chain
+    with chi_max = REF_CHI (the cost grows as chi^3)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    state = workloads.synthetic_state(WL.L, WL.d, WL.chi_max)
-    per_step = 2
+    state = head_state(chi_max=REF_CHI)
     for _ in range(args.warmup):
-        oracle_sample(per_step, state)
+        oracle_update_seconds(state, REF_CHI)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_sample(per_step, state)
-    value = per_step * args.steps / total
+        total += oracle_update_seconds(state, REF_CHI)
+    value = args.steps / total
+    cfg = head_config("fp64")
+    cfg["cpu_sample_chi_max"] = REF_CHI
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config("fp64"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{per_step} three-site updates of the saturated chi=256 state per step"},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "blas": blas_vendor(),
+                             "kind": "oracle",
+                             "sample": f"one U(1)-oracle gate update per step, interior triple of the L=64 d=5 "
+                                       f"charge-labelled saturated chain at chi_max={REF_CHI} (1024 does not fit "
+                                       f"a bounded run)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dense_workload(args):
+    """--workload trunc_L32: the dense form on the L = 32, d = 4, chi = 256 chain alone."""
+    import torch
+    torch.cuda.set_device(0)
+    out = dense_config2(torch.cuda.current_stream(), steps=args.steps, warmup=args.warmup)
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -268,41 +391,36 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
-                    help="mixed: 3xTF32 tensor-core contractions + FP64 SVD (headline); the FP64 path is timed beside it")
+    ap.add_argument("--workload", default="config3_u1", choices=["config3_u1", "trunc_L32"],
+                    help="config3_u1: the headline (L=64 d=5 chi=1024, blocked form); trunc_L32: the dense form alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-simulation batched measurement")
-    ap.add_argument("--workload", default="trunc_L32", choices=sorted(WORKLOADS),
-                    help="trunc_L32 is the measured configuration; parity_L8 is a small case for profiling")
+    ap.add_argument("--no-side", action="store_true", help="skip the FP64 / exact-digit / dense side arms")
     args = ap.parse_args()
-    global WL
-    WL = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "trunc_L32":
+        return run_dense_workload(args)
 
     import torch
     import torch.distributed as dist
-    from paper_2401_05301_gb300 import TEBD
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
     stream = torch.cuda.current_stream()
-    prec = 1 if args.precision == "mixed" else 0
-
-    B, lam, chi = workloads.synthetic_state(WL.L, WL.d, WL.chi_max, seed=workloads.SEED + rank)
-    g = TEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
-             eps_rel=WL.eps_rel, precision=prec, stream=stream.cuda_stream)
-    g.set_state(B, lam)
-    for _ in range(args.warmup):
-        g.step(1)
-        g.measure()
 
     def barrier():
         if ws > 1:
             dist.barrier()
+
+    state = head_state(seed=workloads.SEED + rank)
+    g = make_head(1, stream.cuda_stream, state)
+    for _ in range(args.warmup):
+        g.step(1)
+        g.measure()
 
     # -- device-timed region ------------------------------------------------------
     g.set_option("profile", 1)
@@ -323,55 +441,37 @@ def main():
     prof = g.profile()
     g.set_option("profile", 0)
     t_max = max_over_ranks(ms, ws)
-    value = job_value(gates_per_step(WL.L) * args.steps, ws, t_max / 1e3)
-
-    # -- the plain FP64 path and the FP64-accurate tensor-core path on the same state ----
-    def time_path(precision):
-        gp = TEBD(WL.L, WL.n_max, WL.chi_max, WL.U, WL.J, WL.Jnnn, WL.K, WL.jc, WL.dt, w_cut=WL.w_cut,
-                  eps_rel=WL.eps_rel, precision=precision, stream=stream.cuda_stream)
-        gp.set_state(B, lam)
-        for _ in range(args.warmup):
-            gp.step(1)
-            gp.measure()
-        gp.set_option("profile", 1)
-        barrier()
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            gp.step(1)
-            gp.measure()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fms = max_over_ranks(f0.elapsed_time(f1), ws)
-        pp = gp.profile()
-        gp.close()
-        return {"value": job_value(gates_per_step(WL.L) * args.steps, ws, fms / 1e3), "unit": UNIT,
-                "ms_per_step": fms / args.steps, "classes_ms": {k: round(v[0], 3) for k, v in pp.items()}}
-
-    fp64 = exact = None
-    if prec == 1:
-        fp64 = time_path(0)
-        exact = time_path(2)
-        exact["note"] = ("precision 2: every large product on the exact-digit tensor-core engine "
-                         "(FP64-accurate; parity with the oracle at the FP64 bound)")
+    value = job_value(gates_per_step(HEAD.L) * args.steps, ws, t_max / 1e3)
 
     # -- end to end through the C ABI with host buffers ---------------------------
+    B, lam, q = state
     pinned_B = [torch.from_numpy(np.ascontiguousarray(b)).pin_memory().numpy() for b in B]
     pinned_l = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy() for x in lam]
-    h2d = sum(b.nbytes for b in pinned_B) + sum(x.nbytes for x in pinned_l)
-    d2h = 8 * (WL.L + WL.L - 1)
+    h2d = sum(b.nbytes for b in pinned_B) + sum(x.nbytes for x in pinned_l) + sum(4 * len(x) for x in q)
+    d2h = 8 * (HEAD.L + HEAD.L - 1)
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         g.set_state(pinned_B, pinned_l)
+        g.set_charges(q)
         g.step(1)
         g.measure()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = job_value(gates_per_step(WL.L) * e2e_steps, ws, e2e_s)
+    e2e_value = job_value(gates_per_step(HEAD.L) * e2e_steps, ws, e2e_s)
+    g.close()
+
+    # -- the plain FP64 and FP64-accurate tensor-core paths on the same state -----------
+    fp64 = exact = None
+    if not args.no_side:
+        side = max(1, min(args.steps, SIDE_STEPS))
+        fp64 = side_measurement(time_path, 0, state, stream, side, 1, ws, barrier)
+        exact = side_measurement(time_path, 2, state, stream, side, 1, ws, barrier)
+        if isinstance(exact, dict) and "error" not in exact:
+            exact["note"] = ("precision 2: every large product on the exact-digit tensor-core engine "
+                             "(FP64-accurate; parity with the oracle at the FP64 bound)")
 
     if rank != 0:
         if ws > 1:
@@ -382,57 +482,62 @@ def main():
     # -- roofline of the dominant kernel class ---------------------------------------
     dom = max((k for k in prof if k != "measure"), key=lambda k: prof[k][0])
     dms, dlaunch, dwork = prof[dom]
-    achieved = dwork / (dms / 1e3) / 1e12 if dms > 0 else None
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 CUDA-core rate)",
-                "share_of_step": dms / ms if ms > 0 else None,
-                "classes_ms": {k: round(v[0], 3) for k, v in prof.items()},
-                "classes_tflops": {k: (v[2] / (v[0] / 1e3) / 1e12 if v[0] > 0 and v[2] > 0 else None)
-                                   for k, v in prof.items()}}
-
-    if prec == 1 and prof["contract"][0] > 0:
-        peaks = measured_peaks()
-        bf16 = peaks.get("bf16_tflops")
-        tf32_peak = bf16 * TF32_RATIO if bf16 else 1900.0 * TF32_RATIO
+    achieved = dwork / (dms / 1e3) / 1e12 if dms > 0 and dwork > 0 else None
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops")
+    tf32_peak = (bf16 if bf16 else 1900.0) * TF32_RATIO
+    if dom in ALU_CLASSES or dom not in ("contract",):
+        bound, peak, src = "alu", FP64_PEAK_TFLOPS, \
+            "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 CUDA-core rate; no FP64 entry measured)"
+    else:
+        bound, peak, src = "tensor", tf32_peak, ("measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)" if bf16
+                                                 else "fallback 1.9 PFLOP/s bf16 x 1.1/2.25")
+    roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src,
+                "share_of_step": dms / ms if ms > 0 else None, "launches": dlaunch,
+                "work_note": "algorithmic real flops of the class (Hermitian Gram at half, reduction 16/3 b^3 per "
+                             "charge block of size b) over its CUDA-event time on the handle's stream"}
+    roofline.update(profile_summary(prof))
+    if prof["contract"][0] > 0:
         tc_ach = prof["contract"][2] / (prof["contract"][0] / 1e3) / 1e12
         roofline["tensor_kernel"] = {
-            "kernel": "k_tf32x3 (contract class)", "bound": "tensor", "achieved": tc_ach, "peak": tf32_peak,
-            "unit": "TFLOP/s", "frac": tc_ach / tf32_peak, "traffic": None,
-            "peak_source": ("measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)" if bf16 else
-                            "fallback 1.9 PFLOP/s bf16 x 1.1/2.25"),
+            "kernel": "k_tf32x3 + FP64 gate product (contract class)", "bound": "tensor", "achieved": tc_ach,
+            "peak": tf32_peak, "unit": "TFLOP/s", "frac": tc_ach / tf32_peak, "traffic": None,
             "note": "algorithmic complex flops 8MNK; the 3xTF32 split issues 3x that on the tensor cores"}
 
     served = None
     if not args.no_served and ws == 1:
         served = side_measurement(served_measurement, stream.cuda_stream)
     batched = None
-    if not args.no_batched and ws == 1 and args.workload == "trunc_L32":
+    if not args.no_batched and ws == 1:
         batched = side_measurement(batched_measurement, stream.cuda_stream)
+    config2 = None
+    if not args.no_side and ws == 1:
+        config2 = side_measurement(dense_config2, stream)
 
     cpu = None
     if not args.no_cpu_baseline:
-        n_cpu = 4
-        secs = oracle_sample(n_cpu, (B, lam, chi))
-        cpu = {"value": n_cpu / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n_cpu} three-site updates of the saturated chi=256 state ({secs:.1f} s)"}
+        secs = oracle_update_seconds(state)
+        cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": os.cpu_count(), "blas": blas_vendor(), "kind": "oracle",
+               "sample": f"one U(1)-oracle gate update of the interior triple on sites 31..33 of the same state "
+                         f"(chi_max 1024 on all four bonds), {secs:.1f} s"}
 
     line = {"metric": METRIC,
-            "metric_detail": ("value: mixed path (3xTF32 tensor-core contractions; SVD stage FP64-accurate, its "
-                              "products as exact-digit tensor-core products); fp64_path: the plain FP64 GPU method on "
-                              "the same state; exact_path: FP64-accurate throughout on the tensor cores"
-                              if prec == 1 else "value: plain FP64 GPU method"),
+            "metric_detail": ("value: mixed path of the particle-number-blocked update (3xTF32 tensor-core "
+                              "contractions; decompositions FP64-accurate, their products on the exact-digit "
+                              "tensor-core engine); fp64_path: the plain FP64 GPU method on the same state; "
+                              "exact_path: FP64-accurate throughout on the tensor cores"),
             "value": value, "unit": UNIT, "svds_per_s": 2.0 * value, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+tf32x3",
-            "data": "synthetic", "config": config(args.precision),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+tf32x3",
+            "data": "synthetic", "config": head_config("mixed"),
             "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
             "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "exact_path": exact,
-            "served": served, "batched": batched}
+            "mixed_over_fp64": (value / fp64["value"]) if isinstance(fp64, dict) and fp64.get("value") else None,
+            "dense_config2": config2, "served": served, "batched": batched}
     print(json.dumps(line), flush=True)
-    g.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -75,6 +75,7 @@ struct tebd_ctx {
   bool have_charges = false;
   std::vector<std::vector<int>> q;
   double2* Gblk = nullptr;  // gates restricted to each total-occupation block (u1.cu layout)
+  size_t Gblk_n = 0;        // complex elements of Gblk
   ptebd::U1Work* u1w = nullptr;
   // optional per-class timing (CUDA events on the handle's stream)
   bool prof = false;

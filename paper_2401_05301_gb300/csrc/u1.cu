@@ -468,10 +468,43 @@ int launch_moves(tebd_ctx* c, const std::vector<Move>& mv) {
   return check_launch(c);
 }
 
-Move gather(const void* sv, long long rs, void* pk, long long ldp, int rows, int cols, bool real = false) {
+// Extent checks: every block copy and product the planner emits is checked on the
+// host against the allocation it addresses before anything is launched, so a
+// planning error is reported as TEBD_ERR_STATE instead of reaching past a buffer.
+struct Span {
+  const char* lo = nullptr;
+  const char* hi = nullptr;
+};
+Span span_of(const void* p, size_t bytes) {
+  return Span{static_cast<const char*>(p), static_cast<const char*>(p) + bytes};
+}
+
+// Does the rows x cols block with element (i, j) at p + (i rs + j cs) elements lie inside sp?
+bool fits(const void* p, size_t elem, long long rows, long long cols, long long rs, long long cs, const Span& sp) {
+  if (rows <= 0 || cols <= 0) return true;
+  if (rs < 0 || cs < 0 || !p || !sp.lo) return false;
+  const char* first = static_cast<const char*>(p);
+  const char* last = first + ((rows - 1) * rs + (cols - 1) * cs) * (long long)elem;
+  return first >= sp.lo && last + elem <= sp.hi;
+}
+
+struct Checker {
+  bool ok = true;
+  void need(bool cond, const char* what) {
+    if (!cond && ok) std::fprintf(stderr, "ptebd: blocked-update plan out of bounds (%s)\n", what);
+    ok = ok && cond;
+  }
+};
+
+Move gather(Checker& ck, const char* what, const void* sv, long long rs, const Span& ssp, void* pk, long long ldp,
+            const Span& psp, int rows, int cols, bool real = false) {
+  const size_t e = real ? 8 : 16;
+  ck.need(fits(sv, e, rows, cols, rs, 1, ssp) && fits(pk, e, rows, cols, ldp, 1, psp), what);
   return Move{const_cast<void*>(sv), pk, rs, 1, ldp, rows, cols, 0, real ? 1 : 0};
 }
-Move scatter(void* sv, long long rs, const void* pk, long long ldp, int rows, int cols) {
+Move scatter(Checker& ck, const char* what, void* sv, long long rs, const Span& ssp, const void* pk, long long ldp,
+             const Span& psp, int rows, int cols) {
+  ck.need(fits(sv, 16, rows, cols, rs, 1, ssp) && fits(pk, 16, rows, cols, ldp, 1, psp), what);
   return Move{sv, const_cast<void*>(pk), rs, 1, ldp, rows, cols, 1, 0};
 }
 
@@ -491,6 +524,12 @@ struct Prod {
 };
 
 size_t oz_bytes(const Prod& p) { return oz_workspace_bytes(p.M, p.N, p.K, false); }
+
+void check_prod(Checker& ck, const char* what, const Prod& p, const Span& sa, const Span& sb, const Span& sc) {
+  ck.need(fits(p.A, 16, p.M, p.K, p.lda, 1, sa), what);
+  ck.need(p.opB == OP_C ? fits(p.B, 16, p.N, p.K, p.ldb, 1, sb) : fits(p.B, 16, p.K, p.N, p.ldb, 1, sb), what);
+  ck.need(fits(p.C, 16, p.M, p.N, p.ldc, 1, sc), what);
+}
 
 // engine: 0 FP64 CUDA cores, 1 split 3xTF32 tensor cores, 2 exact-digit tensor cores
 int run_prods(tebd_ctx* c, const std::vector<Prod>& ps, int engine) {
@@ -979,10 +1018,20 @@ int kept_vectors(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases
 
 namespace {
 
+Span site_span(const tebd_ctx* o, int k) { return span_of(o->B[k], 16 * (size_t)o->cap[k] * o->d * o->cap[k + 1]); }
+Span lam_span(const tebd_ctx* o, int k) { return span_of(o->lam[k], 8 * (size_t)o->cap[k]); }
+Span arena_span(const U1Arena& a) { return span_of(a.base, a.cap); }
+
 int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   cudaStream_t s = c->stream;
   const int prec = c->precision;
   // engines: contractions (theta, gate, rebuilds) and the gate product
+  // engines of the contractions (theta~, rebuilds): FP64, split 3xTF32 or exact digits.
+  // The gate product runs on the FP64 CUDA cores in every precision: in the blocked
+  // form its reduction is one occupation block (K = n_Delta <= 19, a single tensor-core
+  // k-step), where the accumulator's round-towards-zero is not averaged over k-steps;
+  // in 3xTF32 it tripled the mixed path's observable error (1.3e-5 against 4.1e-6 at
+  // L = 8, t = 1), for about 1 % of the contraction work.
   const int e_con = prec == 1 ? 1 : (prec == 2 ? 2 : 0);
   const size_t nt = ts.size();
   struct Plan {
@@ -999,7 +1048,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     Runs rl, r1, r2, rr, r1n;
   };
   std::vector<Plan> pl(nt);
-  const int d = c->d, D = c->D;
+  const int d = c->d;
+  Checker ck;
   const SigmaTable sg(d);
   // ---- plan the products and the first cut (sizes from the bond charges)
   for (size_t t = 0; t < nt; ++t) {
@@ -1094,6 +1144,7 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
+      const Span sa = arena_span(T.h->u1w->slots[T.slot].a1);
       if (P.xsize && cudaMemsetAsync(a + P.xoff, 0, P.xsize, s) != cudaSuccess) return fail_cuda(c);
       for (auto& X : P.xb) {
         if (X.K == 0) continue;
@@ -1102,19 +1153,23 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
           const int n = P.rl.count(X.c - s1);
           if (n == 0) continue;
           const long long base = ((long long)P.rl.start(X.c - s1) * d + s1) * T.c1 + k0;
-          mv.push_back(gather(o->B[T.i] + base, (long long)d * T.c1, at<double2>(a, X.oA) + (size_t)X.rs[s1] * K, K, n, K));
+          mv.push_back(gather(ck, "A: B_i", o->B[T.i] + base, (long long)d * T.c1, site_span(o, T.i),
+                              at<double2>(a, X.oA) + (size_t)X.rs[s1] * K, K, sa, n, K));
         }
         for (int s2 = 0; s2 < d; ++s2) {
           const int n = P.r2.count(X.c + s2);
           if (n == 0) continue;
           const long long base = ((long long)k0 * d + s2) * T.c2 + P.r2.start(X.c + s2);
-          mv.push_back(gather(o->B[T.i + 1] + base, (long long)d * T.c2, at<double2>(a, X.oB) + X.cs[s2], X.cols, K, n));
+          mv.push_back(gather(ck, "A: B_i+1", o->B[T.i + 1] + base, (long long)d * T.c2, site_span(o, T.i + 1),
+                              at<double2>(a, X.oB) + X.cs[s2], X.cols, sa, K, n));
         }
         pr.push_back(Prod{at<double2>(a, X.oA), K, at<double2>(a, X.oB), X.cols, at<double2>(a, X.oX), X.cols, X.rows,
                           X.cols, K, OP_N, 1.0, 0});
+        check_prod(ck, "A: product", pr.back(), sa, sa, sa);
         wc += 8.0 * (double)X.rows * X.cols * K;
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
     if (int r = launch_moves(c, mv)) return r;
     if (int r = run_prods(c, pr, e_con)) return r;
@@ -1129,6 +1184,7 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
+      const Span sa = arena_span(T.h->u1w->slots[T.slot].a1);
       if (cudaMemsetAsync(a + P.oTh, 0, 16 * (size_t)std::max<long long>(P.theta_n, 1), s) != cudaSuccess)
         return fail_cuda(c);
       // X block of charge cq, by charge
@@ -1146,16 +1202,19 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
             const Plan::XB* xs = xfind(X.c - s2);
             if (!xs) return TEBD_ERR_STATE;  // cannot happen: the rows and columns exist
             const double2* src = at<double2>(a, xs->oX) + (size_t)xs->rs[s1] * xs->cols + xs->cs[s2];
-            mv.push_back(gather(src, xs->cols, at<double2>(a, X.oXB) + (size_t)X.rs[s1 * d + s2] * K, K, n, K));
+            mv.push_back(gather(ck, "B: X", src, xs->cols, sa, at<double2>(a, X.oXB) + (size_t)X.rs[s1 * d + s2] * K, K,
+                                sa, n, K));
           }
         for (int s3 = 0; s3 < d; ++s3) {
           const int n = P.rr.count(X.c + s3);
           if (n == 0) continue;
           const long long base = ((long long)k0 * d + s3) * T.chr + P.rr.start(X.c + s3);
-          mv.push_back(gather(o->B[T.i + 2] + base, (long long)d * T.chr, at<double2>(a, X.oB2) + X.cs[s3], X.cols, K, n));
+          mv.push_back(gather(ck, "B: B_i+2", o->B[T.i + 2] + base, (long long)d * T.chr, site_span(o, T.i + 2),
+                              at<double2>(a, X.oB2) + X.cs[s3], X.cols, sa, K, n));
         }
         pr.push_back(Prod{at<double2>(a, X.oXB), K, at<double2>(a, X.oB2), X.cols, at<double2>(a, X.oT), X.cols, X.rows,
                           X.cols, K, OP_N, 1.0, 0});
+        check_prod(ck, "B: product", pr.back(), sa, sa, sa);
         wc += 8.0 * (double)X.rows * X.cols * K;
         // scatter theta rows (s1, s2, a) x columns (s3, b) into the compact layout
         for (int s1 = 0; s1 < d; ++s1)
@@ -1168,12 +1227,15 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
               const int dl = s1 + s2 + s3, sgi = sg.idx[(s1 * d + s2) * d + s3];
               const long long cbase = P.cb[dl][al - P.rl.lo()];
               const long long off = P.tD[dl] + (long long)sgi * P.NDl[dl] + cbase;
-              sc.push_back(scatter(at<double2>(a, P.oTh) + off, nb_,
-                                   at<double2>(a, X.oT) + (size_t)X.rs[s1 * d + s2] * X.cols + X.cs[s3], X.cols, na, nb_));
+              sc.push_back(scatter(ck, "B: theta", at<double2>(a, P.oTh) + off, nb_,
+                                   span_of(a + P.oTh, 16 * (size_t)P.theta_n),
+                                   at<double2>(a, X.oT) + (size_t)X.rs[s1 * d + s2] * X.cols + X.cs[s3], X.cols, sa, na,
+                                   nb_));
             }
           }
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
     if (int r = launch_moves(c, mv)) return r;
     if (int r = run_prods(c, pr, e_con)) return r;
@@ -1196,11 +1258,14 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
         if (N == 0) continue;
         pr.push_back(Prod{Gt + sg.gbo[dl], nd, at<double2>(a, P.oTh) + P.tD[dl], N, at<double2>(a, P.oC) + P.tD[dl], N,
                           nd, (int)N, nd, OP_N, 1.0, 0});
+        check_prod(ck, "gate", pr.back(), span_of(o->Gblk, 16 * o->Gblk_n),
+                   span_of(a + P.oTh, 16 * (size_t)P.theta_n), span_of(a + P.oC, 16 * (size_t)P.theta_n));
         wc += 8.0 * (double)nd * nd * N;
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-    if (int r = run_prods(c, pr, prec == 1 ? 1 : 0)) return r;
+    if (int r = run_prods(c, pr, 0)) return r;
   }
   // ---- the first cut: pack its blocks from the compact C
   {
@@ -1210,23 +1275,27 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
+      const Span sa = arena_span(T.h->u1w->slots[T.slot].a1);
       for (CutBlk& B : P.cut1.blk) {
         for (int s1 = 0; s1 < d; ++s1) {
           const int al = B.c - s1, na = P.rl.count(al);
           if (na == 0) continue;
-          mv.push_back(gather(o->lam[T.i] + P.rl.start(al), 1, at<double>(a, B.oLam) + B.rs[s1], 1, na, 1, true));
+          mv.push_back(gather(ck, "cut 1: lambda", o->lam[T.i] + P.rl.start(al), 1, lam_span(o, T.i),
+                              at<double>(a, B.oLam) + B.rs[s1], 1, sa, na, 1, true));
           for (int s2 = 0; s2 < d; ++s2)
             for (int s3 = 0; s3 < d; ++s3) {
               const int be = B.c + s2 + s3, nb_ = P.rr.count(be);
               if (nb_ == 0) continue;
               const int dl = s1 + s2 + s3, sgi = sg.idx[(s1 * d + s2) * d + s3];
               const long long off = P.tD[dl] + (long long)sgi * P.NDl[dl] + P.cb[dl][al - P.rl.lo()];
-              mv.push_back(gather(at<double2>(a, P.oC) + off, nb_,
-                                  at<double2>(a, B.oP) + (size_t)B.rs[s1] * B.n + B.cs[s2 * d + s3], B.n, na, nb_));
+              mv.push_back(gather(ck, "cut 1: C", at<double2>(a, P.oC) + off, nb_,
+                                  span_of(a + P.oC, 16 * (size_t)P.theta_n),
+                                  at<double2>(a, B.oP) + (size_t)B.rs[s1] * B.n + B.cs[s2 * d + s3], B.n, sa, na, nb_));
             }
         }
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_GRAM, 0.0);
     if (int r = launch_moves(c, mv)) return r;
   }
@@ -1250,22 +1319,25 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
+      const Span sa = arena_span(T.h->u1w->slots[T.slot].a1);
       const int chi1 = P.cut1.chi;
       if (cudaMemsetAsync(o->B[T.i], 0, 16 * (size_t)T.chl * d * chi1, s) != cudaSuccess) return fail_cuda(c);
       for (CutBlk& B : P.cut1.blk) {
         if (B.cnt == 0) continue;
         pr.push_back(Prod{at<double2>(a, B.oP), B.n, at<double2>(a, B.oW), B.n, at<double2>(a, B.oOut), B.cnt, B.b,
                           B.cnt, B.n, OP_C, 1.0 / P.cut1.norm, 0});
+        check_prod(ck, "rebuild 1", pr.back(), sa, sa, sa);
         wc += 8.0 * (double)B.b * B.cnt * B.n;
         for (int s1 = 0; s1 < d; ++s1) {
           const int al = B.c - s1, na = P.rl.count(al);
           if (na == 0) continue;
           const long long base = ((long long)P.rl.start(al) * d + s1) * chi1 + B.kst;
-          sc.push_back(scatter(o->B[T.i] + base, (long long)d * chi1, at<double2>(a, B.oOut) + (size_t)B.rs[s1] * B.cnt,
-                               B.cnt, na, B.cnt));
+          sc.push_back(scatter(ck, "rebuild 1: B_i", o->B[T.i] + base, (long long)d * chi1, site_span(o, T.i),
+                               at<double2>(a, B.oOut) + (size_t)B.rs[s1] * B.cnt, B.cnt, sa, na, B.cnt));
         }
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
     if (int r = run_prods(c, pr, e_con)) return r;
     if (int r = launch_moves(c, sc)) return r;
@@ -1304,6 +1376,7 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       Plan& P = pl[t];
       char* a1 = T.h->u1w->slots[T.slot].a1.base;
       char* a = T.h->u1w->slots[T.slot].a2.base;
+      const Span sa1 = arena_span(T.h->u1w->slots[T.slot].a1), sa = arena_span(T.h->u1w->slots[T.slot].a2);
       for (CutBlk& B : P.cut2.blk) {
         for (int s2 = 0; s2 < d; ++s2) {
           const int c1 = B.c - s2, nk = P.r1n.count(c1);
@@ -1312,16 +1385,19 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
           for (const CutBlk& X : P.cut1.blk)
             if (X.c == c1) V = &X;
           if (!V) return TEBD_ERR_STATE;
-          mv.push_back(gather(o->lam[T.i + 1] + V->kst, 1, at<double>(a, B.oLam) + B.rs[s2], 1, nk, 1, true));
+          mv.push_back(gather(ck, "cut 2: lambda", o->lam[T.i + 1] + V->kst, 1, lam_span(o, T.i + 1),
+                              at<double>(a, B.oLam) + B.rs[s2], 1, sa, nk, 1, true));
           for (int s3 = 0; s3 < d; ++s3) {
             const int nb_ = P.rr.count(B.c + s3);
             if (nb_ == 0) continue;
             const double2* src = at<double2>(a1, V->oW) + V->cs[s2 * d + s3];
-            mv.push_back(gather(src, V->n, at<double2>(a, B.oP) + (size_t)B.rs[s2] * B.n + B.cs[s3], B.n, nk, nb_));
+            mv.push_back(gather(ck, "cut 2: V1", src, V->n, sa1, at<double2>(a, B.oP) + (size_t)B.rs[s2] * B.n + B.cs[s3],
+                                B.n, sa, nk, nb_));
           }
         }
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_GRAM, 0.0);
     if (int r = launch_moves(c, mv)) return r;
   }
@@ -1342,6 +1418,7 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a2.base;
+      const Span sa = arena_span(T.h->u1w->slots[T.slot].a2);
       const int chi1 = P.cut1.chi, chi2 = P.cut2.chi;
       if (cudaMemsetAsync(o->B[T.i + 2], 0, 16 * (size_t)chi2 * d * T.chr, s) != cudaSuccess ||
           cudaMemsetAsync(o->B[T.i + 1], 0, 16 * (size_t)chi1 * d * chi2, s) != cudaSuccess)
@@ -1352,21 +1429,23 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
           const int be = B.c + s3, nb_ = P.rr.count(be);
           if (nb_ == 0) continue;
           const long long base = ((long long)B.kst * d + s3) * T.chr + P.rr.start(be);
-          sc.push_back(scatter(o->B[T.i + 2] + base, (long long)d * T.chr, at<double2>(a, B.oW) + B.cs[s3], B.n, B.cnt,
-                               nb_));
+          sc.push_back(scatter(ck, "rebuild 2: B_i+2", o->B[T.i + 2] + base, (long long)d * T.chr, site_span(o, T.i + 2),
+                               at<double2>(a, B.oW) + B.cs[s3], B.n, sa, B.cnt, nb_));
         }
         pr.push_back(Prod{at<double2>(a, B.oP), B.n, at<double2>(a, B.oW), B.n, at<double2>(a, B.oOut), B.cnt, B.b,
                           B.cnt, B.n, OP_C, 1.0 / P.cut2.norm, 0});
+        check_prod(ck, "rebuild 2", pr.back(), sa, sa, sa);
         wc += 8.0 * (double)B.b * B.cnt * B.n;
         for (int s2 = 0; s2 < d; ++s2) {
           const int c1 = B.c - s2, nk = P.r1n.count(c1);
           if (nk == 0) continue;
           const long long base = ((long long)P.r1n.start(c1) * d + s2) * chi2 + B.kst;
-          sc.push_back(scatter(o->B[T.i + 1] + base, (long long)d * chi2, at<double2>(a, B.oOut) + (size_t)B.rs[s2] * B.cnt,
-                               B.cnt, nk, B.cnt));
+          sc.push_back(scatter(ck, "rebuild 2: B_i+1", o->B[T.i + 1] + base, (long long)d * chi2, site_span(o, T.i + 1),
+                               at<double2>(a, B.oOut) + (size_t)B.rs[s2] * B.cnt, B.cnt, sa, nk, B.cnt));
         }
       }
     }
+    if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
     if (int r = run_prods(c, pr, e_con)) return r;
     if (int r = launch_moves(c, sc)) return r;
@@ -1429,6 +1508,7 @@ int u1_build_gate_blocks(tebd_ctx* c, const std::vector<std::complex<double>>& G
   }
   if (c->Gblk) cudaFree(c->Gblk);
   c->Gblk = dst;
+  c->Gblk_n = blk.size();
   return TEBD_OK;
 }
 
