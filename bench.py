@@ -180,11 +180,12 @@ def oracle_update_seconds(state, chi_max: int = HEAD.chi_max, n: int = 1) -> flo
     o = U1TEBD(HEAD.L, HEAD.n_max, chi_max, HEAD.U, HEAD.J, HEAD.Jnnn, HEAD.K, HEAD.jc, HEAD.dt,
                w_cut=HEAD.w_cut, eps_rel=HEAD.eps_rel)
     total = 0.0
-    G = o.gate(31, HEAD.dt / 2)
+    j = HEAD.L // 2 - 1  # the interior triple (sites 31..33 of the 64-site chain)
+    G = o.gate(j, HEAD.dt / 2)
     for _ in range(n):
         o.set_state(B, lam, q)
         t0 = time.perf_counter()
-        o.apply_gate(30, G)
+        o.apply_gate(j - 1, G)
         total += time.perf_counter() - t0
     return total
 
@@ -391,8 +392,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config3_u1", choices=["config3_u1", "trunc_L32"],
-                    help="config3_u1: the headline (L=64 d=5 chi=1024, blocked form); trunc_L32: the dense form alone")
+    ap.add_argument("--workload", default="config3_u1", choices=["config3_u1", "u1_L24", "trunc_L32"],
+                    help="config3_u1: the headline (L=64 d=5 chi=1024, blocked form); u1_L24: the same physics and "
+                         "local sizes on 24 sites (N=12; a small case for profiling); trunc_L32: the dense form alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-simulation batched measurement")
@@ -402,6 +404,11 @@ def main():
         return run_reference(args)
     if args.workload == "trunc_L32":
         return run_dense_workload(args)
+    if args.workload == "u1_L24":
+        global HEAD, N_HEAD
+        HEAD = workloads.Workload("u1_L24_d5_chi1024", L=24, n_max=4, chi_max=1024, U=HEAD.U, J=HEAD.J,
+                                  Jnnn=HEAD.Jnnn, K=HEAD.K, jc=12.5, dt=HEAD.dt, t_end=HEAD.t_end)
+        N_HEAD = 12
 
     import torch
     import torch.distributed as dist

@@ -756,7 +756,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
 }
 
 // One Trotter layer (triples i = residue mod 3, time index tidx) of every
-// simulation in hs, as chunks of at most EIG_MAXP triples in which each
+// simulation in hs, as chunks of at most chunk_max triples in which each
 // simulation uses at most its own number of workspace slots.  c drives.
 int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, int tidx) {
   struct Pending { tebd_ctx* h; int i; };
@@ -764,8 +764,9 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
   for (tebd_ctx* h : hs)
     for (int i = residue; i + 2 < h->L; i += 3) rest.push_back({h, i});
   // Each chunk takes, in order, every pending triple whose simulation still has a free
-  // workspace slot in this chunk, up to EIG_MAXP triples; the triples of a layer are
+  // workspace slot in this chunk, up to chunk_max triples; the triples of a layer are
   // disjoint, so any grouping gives the same (bitwise) result.
+  const int chunk_max = c->u1 ? 64 : CHUNK_MAXP;  // the blocked form has no fixed-size batches
   while (!rest.empty()) {
     std::vector<Triple> ts;
     std::vector<std::pair<tebd_ctx*, int>> used;  // slots taken per simulation in this chunk
@@ -775,7 +776,7 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
       for (auto& u : used)
         if (u.first == p.h) k = &u.second;
       const int taken = k ? *k : 0;
-      if ((int)ts.size() >= EIG_MAXP || taken >= (int)p.h->slots.size()) {
+      if ((int)ts.size() >= chunk_max || taken >= (int)p.h->slots.size()) {
         later.push_back(p);
         continue;
       }
@@ -795,16 +796,21 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
 int run_layer(tebd_ctx* c, int residue, int tidx) { return run_layer_multi(c, {c}, residue, tidx); }
 
 int ensure_measure_ws(tebd_ctx* c) {
-  if (c->mN) return TEBD_OK;
-  const long long capmax = std::max<long long>(1, *std::max_element(c->cap.begin(), c->cap.end()));
-  const long long big = capmax * c->d * capmax;
-  c->mP = dalloc<double2>(c, MEAS_CHUNK * big);
-  c->mQ = dalloc<double2>(c, MEAS_CHUNK * big);
-  c->mX = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
-  c->mY = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
-  c->mC = dalloc<double2>(c, c->L);
-  c->mN = dalloc<double>(c, c->L);
-  if (!c->mP || !c->mQ || !c->mX || !c->mY || !c->mC || !c->mN) return TEBD_ERR_OOM;
+  if (!c->mN) {
+    c->mC = dalloc<double2>(c, c->L);
+    c->mN = dalloc<double>(c, c->L);
+    if (!c->mC || !c->mN) return TEBD_ERR_OOM;
+  }
+  if (c->u1 && c->have_charges) return TEBD_OK;  // the blocked correlators use their own arena
+  if (!c->mP) {
+    const long long capmax = std::max<long long>(1, *std::max_element(c->cap.begin(), c->cap.end()));
+    const long long big = capmax * c->d * capmax;
+    c->mP = dalloc<double2>(c, MEAS_CHUNK * big);
+    c->mQ = dalloc<double2>(c, MEAS_CHUNK * big);
+    c->mX = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
+    c->mY = dalloc<double2>(c, MEAS_CHUNK * capmax * capmax);
+    if (!c->mP || !c->mQ || !c->mX || !c->mY) return TEBD_ERR_OOM;
+  }
   return TEBD_OK;
 }
 
@@ -1208,7 +1214,12 @@ int tebd_measure(tebd_handle h, double* n_out, double* cur_out) {
     h->launches += launch_densities(da.data(), L, h->stream);
     const long long capmax = std::max<long long>(1, *std::max_element(h->cap.begin(), h->cap.end()));
     const long long big = capmax * d * capmax;
-    for (int k0 = 0; k0 < L - 1; k0 += MEAS_CHUNK) {
+    if (h->u1 && h->have_charges) {  // the correlators from the charge blocks
+      if (!h->u1w)
+        if (int r = u1_alloc_slots(h, 0)) return r;
+      if (int r = u1_correlators(h, h->mC)) return r;
+    }
+    for (int k0 = 0; k0 < (h->u1 && h->have_charges ? 0 : L - 1); k0 += MEAS_CHUNK) {
       const int k1 = std::min(L - 1, k0 + MEAS_CHUNK);
       Gemm gx(true, OP_C, OP_N), gy(true, OP_N, OP_C);
       for (int k = k0; k < k1; ++k) {

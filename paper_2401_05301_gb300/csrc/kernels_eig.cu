@@ -911,7 +911,7 @@ int max_m(const EigBatch& b) {
 
 }  // namespace
 
-static_assert(sizeof(EigBatch) < 4000, "kernel parameter block too large");
+static_assert(sizeof(EigBatch) < 32000, "kernel parameter block too large (32 KB on sm_70 and later)");
 
 int eig_trace(const EigBatch& b, cudaStream_t s) {
   if (b.n == 0) return 0;

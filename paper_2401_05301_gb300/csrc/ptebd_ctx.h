@@ -153,5 +153,8 @@ size_t u1_workspace_bytes(const tebd_ctx* c);
 void u1_release(tebd_ctx* c);
 // nslots workspace slots of the blocked form (their arenas grow on first use).
 int u1_alloc_slots(tebd_ctx* c, int nslots);
+// Correlators <b+_k b_{k+1}> of every bond (out: device, L-1 complex) from the charge
+// blocks of the canonical form; needs the handle's charges.
+int u1_correlators(tebd_ctx* h, double2* out);
 
 }  // namespace ptebd

@@ -151,7 +151,12 @@ class Gemm {
 int gemm_launch_single(bool complex_, int opA, int opB, const GemmProb& p, cudaStream_t s);
 
 // ---- eigen-solver for batches of Hermitian matrices (kernels_eig.cu) ---------
-constexpr int EIG_MAXP = 24;
+// Matrices per eigen-solver batch: one cooperative launch of the reduction serves them
+// all, so its per-column grid barriers are paid once per batch (the blocked form
+// decomposes hundreds of charge blocks per layer).
+constexpr int EIG_MAXP = 64;
+// Triples per batch of the dense form (its truncation and gather batches hold 24).
+constexpr int CHUNK_MAXP = 24;
 
 struct EigMat {
   double2* H;        // m x m Hermitian (full storage), row-major, ld = m; reflectors end in rows

@@ -30,6 +30,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <numeric>
 #include <stdexcept>
 #include <vector>
@@ -58,6 +59,7 @@ struct U1Work {
   std::vector<std::pair<char*, char*>> retired[2];  // outgrown staging buffers, freed once idle
   double* h_back = nullptr;                // pinned read-back buffer
   size_t h_back_n = 0;
+  U1Arena meas;                            // blocks of the correlator products
 };
 
 namespace {
@@ -273,6 +275,50 @@ __global__ void k_kept_gather(const KeptGather* __restrict__ kg) {
     const double2 x = make_double2(v.x * inv, v.y * inv);
     G.V[(size_t)i * G.n + j] = x;
     G.W[(size_t)i * G.n + j] = make_double2(1.5 * x.x, 1.5 * x.y);
+  }
+}
+
+// f[i] = lam[i]^2 w[i] (the reduction factors of the correlator's left product)
+__global__ void k_lam2w(const double* __restrict__ lam, const double* __restrict__ w, double* __restrict__ f, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) f[i] = lam[i] * lam[i] * w[i];
+}
+
+// One bond's correlator from its charge blocks: out[bond] = sum over its blocks v of
+// sum_{i, j} X_v[i][j] Y_v[j][i] (X_v: nu x nv, Y_v: nv x nu), in a fixed order.
+struct TraceBlk {
+  const double2* X;
+  const double2* Y;
+  int nu, nv;
+};
+struct TraceBond {
+  int b0, b1;  // blocks [b0, b1) of the list
+  double2* out;
+};
+
+__global__ void k_trace_bonds(const TraceBond* __restrict__ bonds, const TraceBlk* __restrict__ blk) {
+  const TraceBond B = bonds[blockIdx.x];
+  __shared__ double re_sh[32], im_sh[32];
+  double re = 0.0, im = 0.0;
+  for (int q = B.b0; q < B.b1; ++q) {
+    const TraceBlk T = blk[q];
+    const int n = T.nu * T.nv;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int i = e / T.nv, j = e - i * T.nv;
+      const double2 x = T.X[(size_t)i * T.nv + j], y = T.Y[(size_t)j * T.nu + i];
+      re = fma(x.x, y.x, fma(-x.y, y.y, re));
+      im = fma(x.x, y.y, fma(x.y, y.x, im));
+    }
+  }
+  re = warp_sum_d(re);
+  im = warp_sum_d(im);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { re_sh[w] = re; im_sh[w] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0, m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { r += re_sh[k]; m += im_sh[k]; }
+    *B.out = make_double2(r, m);
   }
 }
 
@@ -790,6 +836,38 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
       ev0[q] = j.B->kmax > 0 ? ev[0] : -1.0;
       o += j.B->kmax + 1;
     }
+    // As in the dense form, vectors only for the chi_cap largest eigenvalues of the cut
+    // (merged over its blocks; every value equal to the chi_cap-th is kept too): rule T
+    // keeps at most chi_cap values, so the others would be computed and dropped.
+    {
+      std::vector<std::vector<double>> cand(nc);
+      size_t o2 = 0;
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        const Job& j = jobs[q];
+        for (int k = 0; k < j.B->K; ++k) cand[j.t].push_back(hb[o2 + k]);
+        o2 += j.B->kmax + 1;
+      }
+      std::vector<double> thr(nc, -1.0);
+      for (size_t t = 0; t < nc; ++t) {
+        auto& v = cand[t];
+        const size_t cap = (size_t)cuts[t]->chi_cap;
+        if (v.size() > cap) {
+          std::nth_element(v.begin(), v.begin() + (cap - 1), v.end(), std::greater<double>());
+          thr[t] = v[cap - 1];
+        }
+      }
+      o2 = 0;
+      for (size_t q = 0; q < jobs.size(); ++q) {
+        Job& j = jobs[q];
+        if (thr[j.t] >= 0.0) {
+          const double* ev = hb + o2;
+          int K = 0;
+          while (K < j.B->K && ev[K] >= thr[j.t]) ++K;
+          j.B->K = K;
+        }
+        o2 += j.B->kmax + 1;
+      }
+    }
     // every cut keeps at least one value: its block with the largest eigenvalue
     for (size_t t = 0; t < nc; ++t) {
       int best = -1, any = 0;
@@ -1048,12 +1126,15 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     Runs rl, r1, r2, rr, r1n;
   };
   std::vector<Plan> pl(nt);
-  const int d = c->d;
   Checker ck;
-  const SigmaTable sg(d);
+  // the local dimension of each triple is its own simulation's (a batch may mix them)
+  std::vector<SigmaTable> sgs;
+  for (int dd = 0; dd <= 8; ++dd) sgs.emplace_back(std::max(dd, 1));
   // ---- plan the products and the first cut (sizes from the bond charges)
   for (size_t t = 0; t < nt; ++t) {
     Triple& T = ts[t];
+    [[maybe_unused]] const int d = T.h->d;
+    [[maybe_unused]] const SigmaTable& sg = sgs[d];
     tebd_ctx* o = T.h;
     Plan& P = pl[t];
     T.chl = o->chi[T.i]; T.c1 = o->chi[T.i + 1]; T.c2 = o->chi[T.i + 2]; T.chr = o->chi[T.i + 3];
@@ -1141,6 +1222,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
@@ -1181,6 +1264,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
@@ -1245,9 +1330,11 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   {
     std::vector<Prod> pr;
     double wc = 0.0;
-    const size_t gsz = (size_t)sg.gsz;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
+      const size_t gsz = (size_t)sgs[T.h->d].gsz;
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
@@ -1272,6 +1359,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     std::vector<Move> mv;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
@@ -1316,6 +1405,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a1.base;
@@ -1345,6 +1436,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   // ---- the second cut: R = diag(s) V1^+ with rows (s2, k) and columns (s3, b)
   for (size_t t = 0; t < nt; ++t) {
     Triple& T = ts[t];
+    [[maybe_unused]] const int d = T.h->d;
+    [[maybe_unused]] const SigmaTable& sg = sgs[d];
     tebd_ctx* o = T.h;
     Plan& P = pl[t];
     std::vector<int> q1;
@@ -1372,6 +1465,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     std::vector<Move> mv;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a1 = T.h->u1w->slots[T.slot].a1.base;
@@ -1415,6 +1510,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0;
     for (size_t t = 0; t < nt; ++t) {
       Triple& T = ts[t];
+      [[maybe_unused]] const int d = T.h->d;
+      [[maybe_unused]] const SigmaTable& sg = sgs[d];
       tebd_ctx* o = T.h;
       Plan& P = pl[t];
       char* a = T.h->u1w->slots[T.slot].a2.base;
@@ -1452,6 +1549,8 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   }
   for (size_t t = 0; t < nt; ++t) {
     Triple& T = ts[t];
+    [[maybe_unused]] const int d = T.h->d;
+    [[maybe_unused]] const SigmaTable& sg = sgs[d];
     tebd_ctx* o = T.h;
     Plan& P = pl[t];
     std::vector<int> q1, q2;
@@ -1477,6 +1576,129 @@ int update_chunk_u1(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   const int r = update_chunk_u1_body(c, ts, tidx);
   // the staging buffer of this chunk is reusable once the work issued so far has run
   const int re = stage_end_chunk(c);
+  return r != TEBD_OK ? r : re;
+}
+
+namespace {
+
+// Nearest-neighbour correlators C_k = <b+_k b_{k+1}> of every bond from the charge blocks of
+// the canonical form (eq. (5)): with c, c' indices of the middle bond,
+//   C = sum_{c, c'} X[c, c'] Y[c', c],
+//   X[c, c'] = sum_{a, s} lam_a^2 sqrt(s+1) conj(B_k[a, s+1, c]) B_k[a, s, c'],
+//   Y[c', c] = sum_{t, b} sqrt(t+1) B_{k+1}[c', t+1, b] conj(B_{k+1}[c, t, b]),
+// and X, Y vanish unless q(c) = q(c') + 1: for each charge v of c' one product pair
+// over the rows (a, s) with q(a) + s = v and the columns (t, b) with q(b) = v + 1 + t.
+int correlators_body(tebd_ctx* h, double2* out) {
+  const int L = h->L, d = h->d;
+  Checker ck;
+  struct VB { int k, v, Kx, Ky, nu, nv; size_t oP, oB, oQ, oU, oX, oY, oLam, oF, oW; std::vector<int> rx, cy; };
+  std::vector<VB> vb;
+  Bump bp;
+  for (int k = 0; k + 1 < L; ++k) {
+    const Runs rl = runs_of(h->q[k]), rm = runs_of(h->q[k + 1]), rr = runs_of(h->q[k + 2]);
+    for (int v = rm.lo(); v <= rm.hi(); ++v) {
+      const int nv = rm.count(v), nu = rm.count(v + 1);
+      if (nv == 0 || nu == 0) continue;
+      VB X{};
+      X.k = k; X.v = v; X.nu = nu; X.nv = nv;
+      X.rx.assign(d, 0);
+      X.cy.assign(d, 0);
+      for (int s1 = 0; s1 + 1 < d; ++s1) { X.rx[s1] = X.Kx; X.Kx += rl.count(v - s1); }
+      for (int t = 0; t + 1 < d; ++t) { X.cy[t] = X.Ky; X.Ky += rr.count(v + 1 + t); }
+      if (X.Kx == 0 || X.Ky == 0) continue;
+      X.oP = bp.take(16 * (size_t)X.Kx * nu);
+      X.oB = bp.take(16 * (size_t)X.Kx * nv);
+      X.oQ = bp.take(16 * (size_t)nv * X.Ky);
+      X.oU = bp.take(16 * (size_t)nu * X.Ky);
+      X.oX = bp.take(16 * (size_t)nu * nv);
+      X.oY = bp.take(16 * (size_t)nv * nu);
+      X.oLam = bp.take(8 * (size_t)X.Kx);
+      X.oF = bp.take(8 * (size_t)X.Kx);
+      X.oW = bp.take(8 * (size_t)(X.Kx + X.Ky));
+      vb.push_back(X);
+    }
+  }
+  if (cudaMemsetAsync(out, 0, sizeof(double2) * (L - 1), h->stream) != cudaSuccess) return fail_cuda(h);
+  if (vb.empty()) return TEBD_OK;
+  if (int r = ensure_arena(h, h->u1w->meas, bp.used)) return r;
+  char* a = h->u1w->meas.base;
+  const Span sa = arena_span(h->u1w->meas);
+  std::vector<Move> mv;
+  std::vector<double> wts;  // sqrt(s+1) per row of X's reduction, then sqrt(t+1) per column of Y's
+  std::vector<size_t> woff;
+  for (VB& X : vb) {
+    const int k = X.k, v = X.v, chl = h->chi[k], chm = h->chi[k + 1], chr = h->chi[k + 2];
+    const Runs rl = runs_of(h->q[k]), rm = runs_of(h->q[k + 1]), rr = runs_of(h->q[k + 2]);
+    woff.push_back(wts.size());
+    for (int s1 = 0; s1 + 1 < d; ++s1) {
+      const int na = rl.count(v - s1);
+      if (na == 0) continue;
+      const long long a0 = rl.start(v - s1);
+      mv.push_back(gather(ck, "measure: B_k shifted", h->B[k] + (a0 * d + s1 + 1) * chm + rm.start(v + 1),
+                          (long long)d * chm, site_span(h, k), at<double2>(a, X.oP) + (size_t)X.rx[s1] * X.nu, X.nu, sa,
+                          na, X.nu));
+      mv.push_back(gather(ck, "measure: B_k", h->B[k] + (a0 * d + s1) * chm + rm.start(v), (long long)d * chm,
+                          site_span(h, k), at<double2>(a, X.oB) + (size_t)X.rx[s1] * X.nv, X.nv, sa, na, X.nv));
+      mv.push_back(gather(ck, "measure: lambda", h->lam[k] + a0, 1, lam_span(h, k), at<double>(a, X.oLam) + X.rx[s1],
+                          1, sa, na, 1, true));
+      wts.insert(wts.end(), na, std::sqrt((double)(s1 + 1)));
+    }
+    for (int t = 0; t + 1 < d; ++t) {
+      const int nb_ = rr.count(v + 1 + t);
+      if (nb_ == 0) continue;
+      const long long b0 = rr.start(v + 1 + t);
+      mv.push_back(gather(ck, "measure: B_k+1 shifted", h->B[k + 1] + ((long long)rm.start(v) * d + t + 1) * chr + b0,
+                          (long long)d * chr, site_span(h, k + 1), at<double2>(a, X.oQ) + X.cy[t], X.Ky, sa, X.nv, nb_));
+      mv.push_back(gather(ck, "measure: B_k+1", h->B[k + 1] + ((long long)rm.start(v + 1) * d + t) * chr + b0,
+                          (long long)d * chr, site_span(h, k + 1), at<double2>(a, X.oU) + X.cy[t], X.Ky, sa, X.nu, nb_));
+      wts.insert(wts.end(), nb_, std::sqrt((double)(t + 1)));
+    }
+    (void)chl;
+  }
+  if (!ck.ok) return TEBD_ERR_STATE;
+  if (int r = launch_moves(h, mv)) return r;
+  int err = TEBD_OK;
+  double* dw = stage(h, wts, &err);
+  if (err) return err;
+  Gemm gx(true, OP_C, OP_N), gy(true, OP_N, OP_C);
+  std::vector<TraceBlk> tb;
+  std::vector<TraceBond> bonds;
+  for (size_t i = 0; i < vb.size(); ++i) {
+    VB& X = vb[i];
+    const double* w = dw + woff[i];
+    if (cudaMemcpyAsync(a + X.oW, w, 8 * (size_t)(X.Kx + X.Ky), cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+      return fail_cuda(h);
+    k_lam2w<<<(X.Kx + 255) / 256, 256, 0, h->stream>>>(at<double>(a, X.oLam), at<double>(a, X.oW), at<double>(a, X.oF),
+                                                       X.Kx);
+    h->launches += 1;
+    GemmProb& px = gx.add(X.nu, X.nv, X.Kx, at<double2>(a, X.oP), X.nu, at<double2>(a, X.oB), X.nv,
+                          at<double2>(a, X.oX), X.nv);
+    px.s_red = at<double>(a, X.oF);
+    GemmProb& py = gy.add(X.nv, X.nu, X.Ky, at<double2>(a, X.oQ), X.Ky, at<double2>(a, X.oU), X.Ky,
+                          at<double2>(a, X.oY), X.nu);
+    py.s_red = at<double>(a, X.oW) + X.Kx;
+    if (bonds.empty() || bonds.back().out != out + X.k) bonds.push_back(TraceBond{(int)tb.size(), (int)tb.size(), out + X.k});
+    tb.push_back(TraceBlk{at<double2>(a, X.oX), at<double2>(a, X.oY), X.nu, X.nv});
+    bonds.back().b1 = (int)tb.size();
+  }
+  h->launches += gx.launch(h->stream);
+  h->launches += gy.launch(h->stream);
+  TraceBlk* dtb = stage(h, tb, &err);
+  if (err) return err;
+  TraceBond* dbd = stage(h, bonds, &err);
+  if (err) return err;
+  k_trace_bonds<<<(unsigned)bonds.size(), 256, 0, h->stream>>>(dbd, dtb);
+  h->launches += 1;
+  return check_launch(h);
+}
+
+}  // namespace
+
+int u1_correlators(tebd_ctx* h, double2* out) {
+  if (!h->u1w) return TEBD_ERR_STATE;
+  if (int r = stage_begin_chunk(h)) return r;
+  const int r = correlators_body(h, out);
+  const int re = stage_end_chunk(h);
   return r != TEBD_OK ? r : re;
 }
 
@@ -1516,6 +1738,7 @@ size_t u1_workspace_bytes(const tebd_ctx* c) {
   if (!c->u1w) return 0;
   size_t b = c->u1w->ring_bytes * c->u1w->ring.size() + c->u1w->stage_cap[0] + c->u1w->stage_cap[1];
   for (const U1Slot& s : c->u1w->slots) b += s.a1.cap + s.a2.cap;
+  b += c->u1w->meas.cap;
   return b;
 }
 
@@ -1527,6 +1750,7 @@ void u1_release(tebd_ctx* c) {
     if (s.a2.base) cudaFree(s.a2.base);
   }
   for (void* p : w.ring) cudaFree(p);
+  if (w.meas.base) cudaFree(w.meas.base);
   for (int p = 0; p < 2; ++p) {
     for (auto& b : w.retired[p]) {
       cudaFreeHost(b.first);

@@ -198,7 +198,7 @@ def test_u1_synthetic_state_layer(lib):
     # B_{i+2} = V2^+ of every triple of the last layer has orthonormal rows (a synthetic state's
     # lambdas are not the Schmidt values of its tensors, so its canonical densities need not sum to N)
     from state_checks import canonical_error
-    assert canonical_error([g.get_site(j + 1)[0] for j in range(2, L - 2, 3)]) < 1e-12
+    assert canonical_error([g.get_site(i + 2)[0] for i in range(2, L - 2, 3)]) < 1e-12
     g.close()
 
 
