@@ -447,6 +447,7 @@ def main():
     _, l1 = g.counters()
     prof = g.profile()
     g.set_option("profile", 0)
+    head_bytes = g.device_bytes()
     t_max = max_over_ranks(ms, ws)
     value = job_value(gates_per_step(HEAD.L) * args.steps, ws, t_max / 1e3)
 
@@ -541,6 +542,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": int(l1 - l0),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
+            "device_bytes": head_bytes,
             "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "exact_path": exact,
             "mixed_over_fp64": (value / fp64["value"]) if isinstance(fp64, dict) and fp64.get("value") else None,
             "dense_config2": config2, "served": served, "batched": batched}

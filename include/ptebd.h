@@ -145,6 +145,12 @@ int tebd_layer(tebd_handle h, int residue, int full);
  * it.  Synchronises the handle's stream. */
 int tebd_measure(tebd_handle h, double* n_out, double* cur_out);
 
+/* Serving infrastructure (no counterpart in the paper): the device bytes the
+ * handle holds now (state, gates, workspace, measurement buffers, and the
+ * blocked form's arenas, which grow to the high-water mark of its charge
+ * blocks), written to *bytes. */
+int tebd_device_bytes(tebd_handle h, double* bytes);
+
 /* Current time t = steps * dt, accumulated discarded weight w_total
  * (sum of w over every truncation, Appendix B), and the largest bond
  * dimension.  Any pointer may be NULL. */

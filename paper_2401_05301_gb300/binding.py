@@ -33,6 +33,7 @@ SIGNATURES = {
     "tebd_estimate_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _P_double]),
     "tebd_measure": (_c_int, [_c_void_p, _P_double, _P_double]),
     "tebd_stats": (_c_int, [_c_void_p, _P_double, _P_double, _P_int]),
+    "tebd_device_bytes": (_c_int, [_c_void_p, _P_double]),
     "tebd_bond_dims": (_c_int, [_c_void_p, _P_int]),
     "tebd_get_site": (_c_int, [_c_void_p, _c_int, _P_double, _P_double]),
     "tebd_set_state": (_c_int, [_c_void_p, _P_int, ctypes.POINTER(_P_double), ctypes.POINTER(_P_double)]),
@@ -165,6 +166,11 @@ class TEBD:
         chi = _c_int()
         _check(load().tebd_stats(self._h, ctypes.byref(t), ctypes.byref(w), ctypes.byref(chi)), "tebd_stats")
         return t.value, w.value, chi.value
+
+    def device_bytes(self) -> float:
+        out = _c_double()
+        _check(load().tebd_device_bytes(self._h, ctypes.byref(out)), "tebd_device_bytes")
+        return out.value
 
     def bond_dims(self):
         out = np.empty(self.L + 1, dtype=np.int32)

@@ -174,7 +174,9 @@ int build_gates(tebd_ctx* c) {
     for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
       if (*it == c->G) { c->allocs.erase(it); break; }
     cudaFree(c->G);
+    c->alloc_bytes -= c->G_bytes;
   }
+  c->G_bytes = taus.size() * L2 * DD * sizeof(double2);
   c->G = G;
   return TEBD_OK;
 }
@@ -1251,6 +1253,13 @@ int tebd_measure(tebd_handle h, double* n_out, double* cur_out) {
   } catch (...) {
     return TEBD_ERR_OOM;
   }
+  return TEBD_OK;
+}
+
+int tebd_device_bytes(tebd_handle h, double* bytes) {
+  CHECK_HANDLE(h);
+  if (!bytes) return TEBD_ERR_ARG;
+  *bytes = (double)(h->alloc_bytes + h->Gblk_n * sizeof(double2) + u1_workspace_bytes(h));
   return TEBD_OK;
 }
 

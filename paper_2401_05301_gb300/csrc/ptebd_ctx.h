@@ -55,6 +55,7 @@ struct tebd_ctx {
   std::vector<double2*> B;
   std::vector<double*> lam;
   double2* G = nullptr;
+  size_t G_bytes = 0;
   double2** dB = nullptr;
   double** dlam = nullptr;
   int* d_status = nullptr;
@@ -69,6 +70,7 @@ struct tebd_ctx {
   double w_total = 0.0;
   long long steps = 0, gate_updates = 0, launches = 0;
   std::vector<void*> allocs;
+  size_t alloc_bytes = 0;  // device bytes of allocs
   // particle-number (U(1)) blocked form: option "u1"; q[k] = boson count left of
   // bond k for each Schmidt index, non-decreasing (each charge one contiguous run)
   bool u1 = false;
@@ -132,6 +134,7 @@ T* dalloc(tebd_ctx* c, size_t count) {
     return nullptr;
   }
   c->allocs.push_back(p);
+  c->alloc_bytes += count * sizeof(T);
   return static_cast<T*>(p);
 }
 
