@@ -268,81 +268,127 @@ def dense_config2(stream, steps: int = 2, warmup: int = 1):
     return out
 
 
-def served_requests(n: int = 24, rate: float = 8.0):
-    """Seeded Poisson stream shaped like the serving workload, scaled to run in about a
-    minute: 90% chains like the L=64, d=5 mixed-precision one (here L=24, chi_max=32,
-    t = 0.2) and 10% larger d=4 jobs (L=40, chi_max=64, t = 0.4)."""
+SERVE_REQUESTS = 24      # config 5 streams 500; scaled to fit a bounded run
+SERVE_STEPS = (16, 8)    # steps of the headline-style / large requests (config 5: to t = 8 / t = 6)
+SERVE_SLOTS = 4          # workspace slots per request (more requests fit the budget)
+SERVE_CONCURRENT = 6     # the HBM budget admits about this many headline-style requests at once
+
+
+def serve_stream(rate: float, seed: int = workloads.SEED, n: int = SERVE_REQUESTS, blocked: bool = True,
+                 at_once: bool = False):
+    """Config 5's request mix, scaled: 90% chains like the headline (L=64, d=5, chi_max=1024, U=3,
+    J_NNN=0.1, K=0.003 about j_c=32.5, dt=0.005) and 10% large jobs (L=100, d=4, chi_max=2048, U=5,
+    J_NNN=0.1, K=0.002 about j_c=50.5, dt=0.01), each from its CDW state, measured every 4 steps.
+    Seeded draws: the exponential inter-arrival times first, then the request types."""
     from paper_2401_05301_gb300 import serving
-
-    def make(i, t, rng):
-        if rng.uniform() < 0.9:
-            L = 24
-            return serving.Request(rid=i, arrival=t, L=L, n_max=4, chi_max=32, U=3.0, J=1.0, Jnnn=0.1, K=0.003,
-                                   jc=(L + 1) / 2, dt=0.005, n_steps=40, measure_every=10)
-        L = 40
-        return serving.Request(rid=i, arrival=t, L=L, n_max=3, chi_max=64, U=5.0, J=1.0, Jnnn=0.1, K=0.002,
-                               jc=(L + 1) / 2, dt=0.01, n_steps=40, measure_every=10)
-
-    return serving.poisson_requests(n, rate, workloads.SEED, make)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=n) if rate > 0 else np.zeros(n)
+    large = rng.uniform(size=n) >= 0.9
+    out, t = [], 0.0
+    for i in range(n):
+        t = 0.0 if at_once else t + float(gaps[i])
+        if large[i]:
+            L = 100
+            out.append(serving.Request(rid=i, arrival=t, L=L, n_max=3, chi_max=2048, U=5.0, J=1.0, Jnnn=0.1,
+                                       K=0.002, jc=(L + 1) / 2, dt=0.01, n_steps=SERVE_STEPS[1], measure_every=4,
+                                       max_slots=SERVE_SLOTS, u1=blocked))
+        else:
+            wl = HEAD
+            out.append(serving.Request(rid=i, arrival=t, L=wl.L, n_max=wl.n_max, chi_max=wl.chi_max, U=wl.U,
+                                       J=wl.J, Jnnn=wl.Jnnn, K=wl.K, jc=wl.jc, dt=wl.dt, n_steps=SERVE_STEPS[0],
+                                       measure_every=4, max_slots=SERVE_SLOTS, u1=blocked))
+    return out
 
 
 def served_measurement(stream_ptr):
-    """Continuous batching (mixed path) vs one-at-a-time plain FP64 on the same stream."""
-    from paper_2401_05301_gb300 import serving
-    reqs = served_requests()
-    srv = serving.Server(40e9, precision=1, stream_ptr=stream_ptr)
-    batched = serving.latency_stats(srv.run(reqs))
-    fifo_srv = serving.Server(40e9, precision=0, max_active=1, stream_ptr=stream_ptr)
-    fifo = serving.latency_stats(fifo_srv.run(reqs))
-    return {"requests": len(reqs), "arrival_rate_per_s": 8.0,
-            "workload": "Poisson stream: 90% L=24 d=5 chi_max=32 t=0.2, 10% L=40 d=4 chi_max=64 t=0.4",
-            "continuous_batching_mixed": batched, "one_at_a_time_fp64": fifo,
-            "peak_active": srv.peak_active}
+    """Continuous batching of the blocked mixed-precision form under an HBM budget that admits
+    about SERVE_CONCURRENT headline-style requests at once, against one-at-a-time plain FP64
+    (the dense form, precision 0) on the same stream.  Capacity = requests/s with every request
+    waiting at t = 0; the Poisson streams then offer 0.5, 0.9 and 1.2 of it."""
+    from paper_2401_05301_gb300 import binding, serving
+    small = binding.estimate_bytes(HEAD.L, HEAD.n_max, HEAD.chi_max, SERVE_SLOTS, 1, u1=True)
+    large = binding.estimate_bytes(100, 3, 2048, SERVE_SLOTS, 1, u1=True)
+    budget = max(SERVE_CONCURRENT * small, 1.05 * large)
+
+    def serve(reqs, precision=1, max_active=64, hbm=budget):
+        srv = serving.Server(hbm, precision=precision, max_active=max_active, stream_ptr=stream_ptr)
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        return serving.latency_stats(res), time.perf_counter() - t0, srv
+
+    cap_stats, cap_s, _ = serve(serve_stream(0.0, at_once=True))
+    capacity = SERVE_REQUESTS / cap_s
+    loads = {}
+    for load in (0.5, 0.9, 1.2):
+        st, wall, srv = serve(serve_stream(load * capacity))
+        st["peak_active"] = srv.peak_active
+        st["peak_budget_fraction"] = srv.peak_used / budget
+        loads[f"{load:g}"] = st
+    fifo_stats, fifo_s, _ = serve(serve_stream(0.9 * capacity, blocked=False), precision=0, max_active=1,
+                                  hbm=float("inf"))
+    return {"workload": (f"config 5's mix scaled: {SERVE_REQUESTS} Poisson requests (500 in config 5), 90% "
+                         f"L=64 d=5 chi_max=1024 for {SERVE_STEPS[0]} steps (t=8 in config 5), 10% L=100 d=4 "
+                         f"chi_max=2048 for {SERVE_STEPS[1]} steps (t=6), each from its CDW state, "
+                         f"{SERVE_SLOTS} workspace slots per request"),
+            "hbm_budget_bytes": budget, "footprint_bytes": {"headline_style": small, "large": large},
+            "capacity_requests_per_s": capacity, "capacity_run": cap_stats,
+            "continuous_batching_mixed_blocked": loads,
+            "one_at_a_time_fp64_dense_at_0.9": {**fifo_stats, "wall_s": fifo_s}}
 
 
-def batched_measurement(stream_ptr, steps: int = 10):
-    """The 48 seeded simulations of the batched configuration (L in 16..64, chi_max in 64..512, d = 4),
-    from their CDW product states: `tebd_batch_step` over all of them (one workspace slot each, so a
-    layer's triples of many simulations share every grouped launch) against stepping each alone with
-    its own default workspace.  Both start after one untimed step; mixed path."""
+def batched_measurement(stream_ptr, steps: int = 2):
+    """Config 4: the 48 seeded simulations (L in 16..64, chi_max in 64..512, d = 4, seeded U, J_NNN,
+    K; j_c = (L+1)/2), warm-started at chi_max: each from the charge-labelled synthetic saturated
+    state of its chain at half filling (N = L/2), blocked form, mixed precision.  One
+    `tebd_batch_step` over all 48 (every stage of a layer is one grouped launch over the triples of
+    many simulations) against stepping each alone; both after one untimed step."""
     import torch
     from paper_2401_05301_gb300 import TEBD, batch_step
     wls = workloads.batch48()
+    states = [workloads.synthetic_state_u1(w.L, w.d, w.chi_max, w.L // 2, seed=workloads.SEED + 1000 + i)
+              for i, w in enumerate(wls)]
 
-    def make(w, slots):
-        g = TEBD(w.L, w.n_max, w.chi_max, w.U, w.J, w.Jnnn, w.K, w.jc, w.dt, precision=1, stream=stream_ptr)
-        if slots:
-            g.set_option("max_slots", slots)
-        g.init_product(workloads.cdw(w.L))
+    def make(w, st):
+        g = TEBD(w.L, w.n_max, w.chi_max, w.U, w.J, w.Jnnn, w.K, w.jc, w.dt, precision=1, stream=stream_ptr,
+                 u1=True)
+        B, lam, q = st
+        g.set_state(B, lam)
+        g.set_charges(q)
         return g
 
-    sims = [make(w, 1) for w in wls]
+    sims = [make(w, st) for w, st in zip(wls, states)]
     batch_step(sims, 1)
     torch.cuda.synchronize()
     g0 = sum(g.counters()[0] for g in sims)
+    l0 = sims[0].counters()[1]
     t = time.perf_counter()
     batch_step(sims, steps)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t
     gb = sum(g.counters()[0] for g in sims) - g0
+    lb = sims[0].counters()[1] - l0  # the first handle drives the batch and counts its launches
     for g in sims:
         g.close()
-    ta, ga = 0.0, 0
-    for w in wls:
-        g = make(w, 0)
+    ta, ga, la = 0.0, 0, 0
+    for w, st in zip(wls, states):
+        g = make(w, st)
         g.step(1)
         torch.cuda.synchronize()
-        c0 = g.counters()[0]
+        c0, k0 = g.counters()
         t = time.perf_counter()
         g.step(steps)
         torch.cuda.synchronize()
         ta += time.perf_counter() - t
-        ga += g.counters()[0] - c0
+        c1, k1 = g.counters()
+        ga += c1 - c0
+        la += k1 - k0
         g.close()
-    return {"workload": f"48 seeded simulations (L 16..64, chi_max 64..512, d=4) from CDW product states, "
-                        f"{steps} steps after one untimed step", "unit": UNIT,
+    return {"workload": f"48 seeded simulations (L 16..64, chi_max 64..512, d=4, N=L/2) from their "
+                        f"charge-labelled synthetic saturated states, {steps} steps after one untimed step, "
+                        f"blocked form, mixed precision", "unit": UNIT,
             "batched_value": gb / tb, "batched_s": tb, "alone_value": ga / ta, "alone_s": ta,
-            "gate_updates": gb}
+            "gate_updates": gb, "launches_per_step_batched": lb / steps, "launches_per_step_alone": la / steps,
+            "speedup": (gb / tb) / (ga / ta)}
 
 
 def run_reference(args):

@@ -121,6 +121,14 @@ int tebd_step(tebd_handle h, int n_steps);
  * table is counted for trotter_order 2 (order 4 holds twice as many gates). */
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
+/* tebd_estimate_bytes for a handle of the particle-number-blocked form (option
+ * "u1"): dense site tensors, gates and their occupation blocks, and per workspace
+ * slot an arena allowance for a saturated local update (the blocked arenas grow
+ * with the charge blocks; the allowance is a fixed fraction of the dense theta,
+ * 16 chi_max^2 d^3 bytes, calibrated on a saturated chi = 1024, d = 5 state).
+ * Host-only arithmetic.  Serving infrastructure (no counterpart in the paper). */
+int tebd_estimate_bytes_u1(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
+
 /* Batched form (an addition: the paper runs one chain per job, Sec. II B, IV):
  * advance n distinct handles (simulations with any L, n_max,
  * chi_max and parameters) by n_steps full steps together.  Within every

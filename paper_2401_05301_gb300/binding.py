@@ -31,6 +31,7 @@ SIGNATURES = {
     "tebd_layer": (_c_int, [_c_void_p, _c_int, _c_int]),
     "tebd_batch_step": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, _c_int]),
     "tebd_estimate_bytes": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _P_double]),
+    "tebd_estimate_bytes_u1": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _P_double]),
     "tebd_measure": (_c_int, [_c_void_p, _P_double, _P_double]),
     "tebd_stats": (_c_int, [_c_void_p, _P_double, _P_double, _P_int]),
     "tebd_device_bytes": (_c_int, [_c_void_p, _P_double]),
@@ -87,10 +88,16 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(_P_double)
 
 
-def estimate_bytes(L, n_max, chi_max, max_slots=0, precision=0) -> float:
-    """Device bytes a simulation of these sizes will hold (tebd_estimate_bytes)."""
+def estimate_bytes(L, n_max, chi_max, max_slots=0, precision=0, u1=False) -> float:
+    """Device bytes a simulation of these sizes will hold (tebd_estimate_bytes, or
+    tebd_estimate_bytes_u1 for the particle-number-blocked form)."""
     out = _c_double()
-    _check(load().tebd_estimate_bytes(L, n_max, chi_max, max_slots, precision, ctypes.byref(out)), "tebd_estimate_bytes")
+    if u1:
+        _check(load().tebd_estimate_bytes_u1(L, n_max, chi_max, max_slots, precision, ctypes.byref(out)),
+               "tebd_estimate_bytes_u1")
+    else:
+        _check(load().tebd_estimate_bytes(L, n_max, chi_max, max_slots, precision, ctypes.byref(out)),
+               "tebd_estimate_bytes")
     return out.value
 
 

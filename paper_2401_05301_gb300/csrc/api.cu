@@ -85,6 +85,13 @@ int ensure_pinned(tebd_ctx* c, size_t n) {
 
 namespace {
 
+// Arena bytes of one blocked local update at saturation, as a fraction of the dense
+// theta (16 chi^2 d^3): the blocked arenas hold the compact theta and C (each at most
+// max_Delta n_Delta / d^3 of the dense one), the packed blocks of both cuts and their
+// eigen-solver buffers; measured at the chi = 1024, d = 5 headline state (see the
+// bench's device_bytes) and rounded up.
+constexpr double U1_ARENA_FRACTION = 0.5;
+
 int max_triples_per_layer(int L) {
   int best = 0;
   for (int r = 0; r < 3; ++r) {
@@ -1150,6 +1157,27 @@ int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precis
   if (max_slots > 0) slots = std::min(slots, max_slots);
   b += slots * slot_bytes_for(capmax, d, chi_max, precision);
   b += 16.0 * MEAS_CHUNK * (2.0 * capmax * d * capmax + 2.0 * capmax * capmax) + 24.0 * L;  // measurement
+  *bytes = b;
+  return TEBD_OK;
+}
+
+int tebd_estimate_bytes_u1(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes) {
+  if (!bytes || L < 3 || n_max < 1 || n_max > 7 || chi_max < 1 || max_slots < 0) return TEBD_ERR_ARG;
+  if (precision < 0 || precision > 2) return TEBD_ERR_ARG;
+  const int d = n_max + 1, D = d * d * d;
+  const std::vector<int> cap = bond_caps(L, d, chi_max);
+  double b = 0.0;
+  long long capmax = 1;
+  for (int k = 0; k < L; ++k) b += 16.0 * cap[k] * d * cap[k + 1];  // dense site tensors
+  for (int k = 0; k <= L; ++k) {
+    b += 8.0 * cap[k];
+    capmax = std::max<long long>(capmax, cap[k]);
+  }
+  b += 16.0 * 2.0 * (L - 2) * (double)D * D * 2.0;  // gate table and its occupation blocks (bounded by the table)
+  int slots = std::min(max_triples_per_layer(L), MAX_SLOTS);
+  if (max_slots > 0) slots = std::min(slots, max_slots);
+  b += slots * U1_ARENA_FRACTION * 16.0 * (double)capmax * capmax * D;
+  b += 40.0 * L + 64.0e6;  // measurement buffers, staging, exact-digit ring
   *bytes = b;
   return TEBD_OK;
 }

@@ -176,6 +176,80 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   if (active && sub == 0) M.evals[j] = 0.5 * (lo + hi);
 }
 
+// ---- eigenvalue counts of a cut -------------------------------------------------------
+// A cut's spectrum is the union of its matrices' (the charge blocks of one truncated
+// SVD).  Rule T keeps at most `target` values of the cut, so each matrix needs only
+// its eigenvalues above the cut's target-th largest one (and above the floor
+// floor_rel x the cut's trace).  One block per cut finds that threshold by
+// multisection on the summed Sturm counts: P points per matrix per iteration, each
+// iteration shrinking the bracket by P + 1, then writes per matrix the number of
+// its eigenvalues at or above the bracket's lower end (capped by kmax).
+__device__ __forceinline__ int count_at_or_above(const EigMat& M, double x) { return M.m - sturm_count(M.d, M.e, M.m, x); }
+
+__global__ void __launch_bounds__(1024) k_cut_counts(const ThrCut* __restrict__ cuts) {
+  const ThrCut C = cuts[blockIdx.x];
+  __shared__ double sh[33];
+  __shared__ int cnt[64];
+  __shared__ double lo_sh, hi_sh;
+  __shared__ int go_sh;
+  // the cut's trace and an upper bound of its spectrum (Gershgorin)
+  double tr = 0.0, up = 0.0;
+  for (int i = threadIdx.x; i < C.n; i += blockDim.x) tr += *C.mats[i].trace;
+  for (int i = 0; i < C.n; ++i) {
+    const EigMat& M = C.mats[i];
+    for (int r = threadIdx.x; r < M.m; r += blockDim.x) {
+      double g = M.d[r];
+      if (r > 0) g += fabs(M.e[r - 1]);
+      if (r < M.m - 1) g += fabs(M.e[r]);
+      up = fmax(up, g);
+    }
+  }
+  tr = block_sum(tr, sh);
+  up = -block_min(-up, sh);
+  const double floor_v = C.floor_rel * tr;
+  // how many eigenvalues lie at or above the floor
+  if (threadIdx.x == 0) cnt[0] = 0;
+  __syncthreads();
+  {
+    int mine = 0;
+    for (int i = threadIdx.x; i < C.n; i += blockDim.x) mine += min(C.mats[i].kmax, count_at_or_above(C.mats[i], floor_v));
+    atomicAdd(&cnt[0], mine);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    lo_sh = floor_v;
+    hi_sh = fmax(up, floor_v) * (1.0 + 4.0 * DBL_EPSILON) + DBL_MIN;
+    go_sh = cnt[0] > C.target;
+  }
+  __syncthreads();
+  const int P = max(1, min(63, (int)blockDim.x / max(C.n, 1)));
+  for (int it = 0; it < 40 && go_sh; ++it) {
+    const double lo = lo_sh, hi = hi_sh;
+    if (threadIdx.x < P) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int pidx = threadIdx.x; pidx < C.n * P; pidx += blockDim.x) {
+      const int i = pidx / P, j = pidx - i * P;
+      const double x = lo + (hi - lo) * (double)(j + 1) / (double)(P + 1);
+      atomicAdd(&cnt[j], min(C.mats[i].kmax, count_at_or_above(C.mats[i], x)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int jb = -1;  // the last point still holding at least `target` values
+      for (int j = 0; j < P; ++j)
+        if (cnt[j] >= C.target) jb = j;
+      const double nlo = (jb >= 0) ? lo + (hi - lo) * (double)(jb + 1) / (double)(P + 1) : lo;
+      const double nhi = (jb + 1 < P) ? lo + (hi - lo) * (double)(jb + 2) / (double)(P + 1) : hi;
+      lo_sh = nlo;
+      hi_sh = nhi;
+      go_sh = (nhi - nlo) > 4.0 * DBL_EPSILON * fmax(fabs(nhi), DBL_MIN);
+    }
+    __syncthreads();
+  }
+  const double x = lo_sh;
+  for (int i = threadIdx.x; i < C.n; i += blockDim.x)
+    C.kmax_out[i] = min(C.mats[i].kmax, count_at_or_above(C.mats[i], x));
+}
+
 // ---- inverse iteration ----------------------------------------------------------------
 __device__ __forceinline__ double hash_uniform(unsigned long long a, unsigned long long b) {
   unsigned long long z = a * 0x9E3779B97F4A7C15ull + b * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
@@ -703,7 +777,9 @@ __device__ void phase1_regs(const EigMat& M, int k, int j, double* sh, double2* 
 //           for the part of column k's own term that needs alpha.
 // After the panel, the caller applies A -= V W^+ + W V^+ to rows and columns >= k1
 // as one Hermitian rank-2*NB matrix product.
-__global__ void __launch_bounds__(TD_THREADS) k_tridiag_panel(const __grid_constant__ EigBatch b, int k0, int k1) {
+// Three blocks per SM (80 registers, a 64-byte spill): the reduction is latency bound
+// (barrier and scoreboard stalls), so the extra resident warps hide part of it.
+__global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_constant__ EigBatch b, int k0, int k1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double2 acc_sh[TD_WARPS][TD_STRIP];
   __shared__ double2 xy_sh[2 * TD_NB];
@@ -928,7 +1004,7 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_panel, TD_THREADS, 0);
-    grid = std::max(1, sms * std::min(per_sm, 2));
+    grid = std::max(1, sms * std::min(per_sm, 3));
   }
   int launches = 0;
   for (int k0 = 0; k0 < mm; k0 += TD_NB) {
@@ -988,6 +1064,12 @@ size_t eig_panel_doubles2(int m) {
   return bt_offset(m) + 2 * BT * BT + (size_t)2 * m * BT;
 }
 static_assert(BT == 2 * TD_NB && TD_STRIP == 32 && TD_CHUNK == 256, "bt_offset() mirrors the panel layout");
+
+int eig_cut_counts(const ThrCut* cuts_dev, int ncuts, cudaStream_t s) {
+  if (ncuts <= 0) return 0;
+  k_cut_counts<<<ncuts, 1024, 0, s>>>(cuts_dev);
+  return 1;
+}
 
 int eig_bisect(const EigBatch& b, cudaStream_t s) {
   if (b.n == 0) return 0;

@@ -195,6 +195,16 @@ int eig_trace(const EigBatch& b, cudaStream_t s);
 int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* status, cudaStream_t s);
 size_t eig_panel_doubles2(int m);  // complex elements of EigMat::pan for an m x m matrix
 int eig_bisect(const EigBatch& b, cudaStream_t s);
+// Eigenvalues needed per matrix of a cut (matrices whose spectra are merged): those at
+// or above the cut's target-th largest eigenvalue and the floor floor_rel x the cut's
+// trace, at most kmax.  The tridiagonal (d, e) and trace of every matrix are in place.
+struct ThrCut {
+  const EigMat* mats;  // device array of the cut's matrices
+  int n, target;
+  double floor_rel;
+  int* kmax_out;       // device [n]
+};
+int eig_cut_counts(const ThrCut* cuts_dev, int ncuts, cudaStream_t s);
 // Inverse iteration on T for eigenvalues 0..K-1, Newton-Schulz orthonormalisation,
 // and back-transformation U = Q Z: in the mixed path in blocks of 64 reflectors
 // (compact WY form, block products on the exact-digit engine), in the FP64 path

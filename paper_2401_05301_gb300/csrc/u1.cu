@@ -48,8 +48,10 @@ struct U1Slot {
 
 struct U1Work {
   std::vector<U1Slot> slots;
-  std::vector<void*> ring;  // digit workspaces of the exact-digit engine, one per concurrent problem
-  size_t ring_bytes = 0;
+  // digit workspaces of the exact-digit engine, one per problem of a launch: OZ_MAXP for
+  // the block products (sized for the largest), EIG_MAXP for the eigen-solver's products
+  std::vector<void*> ring, ering;
+  size_t ring_bytes = 0, ering_bytes = 0;
   char* h_stage[2] = {nullptr, nullptr};  // pinned staging of descriptors, by chunk parity
   char* d_stage[2] = {nullptr, nullptr};
   size_t stage_cap[2] = {0, 0};
@@ -60,11 +62,14 @@ struct U1Work {
   double* h_back = nullptr;                // pinned read-back buffer
   size_t h_back_n = 0;
   U1Arena meas;                            // blocks of the correlator products
+  int* d_counts = nullptr;                 // eigenvalues needed per block of a batch of cuts
+  size_t d_counts_n = 0;
 };
 
 namespace {
 
-constexpr int RING = EIG_MAXP;  // >= OZ_MAXP: distinct workspaces within any one launch
+constexpr int RING = OZ_MAXP;    // problems of one exact-digit launch
+constexpr int ERING = EIG_MAXP;  // matrices of one eigen-solver batch
 constexpr int MV_TILE = 4096;   // elements per block of the move kernel
 constexpr int TR_THREADS = 1024;
 
@@ -398,29 +403,31 @@ int ensure_arena(tebd_ctx* c, U1Arena& a, size_t bytes) {
   return TEBD_OK;
 }
 
-int ensure_ring(tebd_ctx* c, size_t bytes) {
-  U1Work& w = *c->u1w;
-  if (w.ring_bytes >= bytes && (int)w.ring.size() == RING) return TEBD_OK;
-  if (!w.ring.empty()) {
+int grow_ring(tebd_ctx* c, std::vector<void*>& ring, size_t& have, int count, size_t bytes) {
+  if (have >= bytes && (int)ring.size() == count) return TEBD_OK;
+  if (!ring.empty()) {
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail_cuda(c);
-    for (void* p : w.ring) cudaFree(p);
+    for (void* p : ring) cudaFree(p);
   }
-  w.ring.clear();
-  w.ring_bytes = 0;
+  ring.clear();
+  have = 0;
   const size_t want = align256(bytes + bytes / 4);
-  for (int i = 0; i < RING; ++i) {
+  for (int i = 0; i < count; ++i) {
     void* p = nullptr;
     if (cudaMalloc(&p, want) != cudaSuccess) {
       cudaGetLastError();
-      for (void* q : w.ring) cudaFree(q);
-      w.ring.clear();
+      for (void* q : ring) cudaFree(q);
+      ring.clear();
       return TEBD_ERR_OOM;
     }
-    w.ring.push_back(p);
+    ring.push_back(p);
   }
-  w.ring_bytes = want;
+  have = want;
   return TEBD_OK;
 }
+
+int ensure_ring(tebd_ctx* c, size_t bytes) { return grow_ring(c, c->u1w->ring, c->u1w->ring_bytes, RING, bytes); }
+int ensure_ering(tebd_ctx* c, size_t bytes) { return grow_ring(c, c->u1w->ering, c->u1w->ering_bytes, ERING, bytes); }
 
 int ensure_back(tebd_ctx* c, size_t n) {
   U1Work& w = *c->u1w;
@@ -741,7 +748,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
     }
   std::stable_sort(jobs.begin(), jobs.end(), [](const Job& x, const Job& y) { return x.B->b > y.B->b; });
   if (mixed)
-    if (int r = ensure_ring(c, ews)) return r;
+    if (int r = ensure_ering(c, ews)) return r;
   auto mat = [&](const Job& j) {
     char* a = bases[j.t];
     CutBlk& B = *j.B;
@@ -756,7 +763,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
   };
   void* ozw[EIG_MAXP] = {};
   if (mixed)
-    for (int i = 0; i < EIG_MAXP; ++i) ozw[i] = c->u1w->ring[i];
+    for (int i = 0; i < EIG_MAXP; ++i) ozw[i] = c->u1w->ering[i];
   {
     double w = 0.0;
     for (const Job& j : jobs) w += 16.0 / 3.0 * std::pow((double)j.B->b, 3);
@@ -778,9 +785,55 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
   }
   {
     ProfScope ps(c, TEBD_PROF_BISECT, 0.0);
-    for (size_t g0 = 0; g0 < jobs.size(); g0 += EIG_MAXP) {
+    // eigenvalues needed per block: at most the cut's chi_cap largest, above the floor
+    std::vector<EigMat> em;
+    std::vector<ThrCut> tcut(nc);
+    std::vector<CutBlk*> order;
+    for (size_t t = 0; t < nc; ++t) {
+      tcut[t].n = (int)cuts[t]->blk.size();
+      tcut[t].target = cuts[t]->chi_cap;
+      tcut[t].floor_rel = std::max(0.01 * cuts[t]->eps_rel, 1e-15);
+      for (CutBlk& B : cuts[t]->blk) {
+        em.push_back(mat(Job{t, &B}));
+        order.push_back(&B);
+      }
+    }
+    U1Work& w = *c->u1w;
+    if (w.d_counts_n < em.size()) {
+      if (w.d_counts) cudaFree(w.d_counts);  // idle: only used between the synchronisations below
+      w.d_counts = nullptr;
+      w.d_counts_n = 0;
+      if (cudaMalloc(&w.d_counts, sizeof(int) * std::max<size_t>(em.size(), 64) * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return TEBD_ERR_OOM;
+      }
+      w.d_counts_n = std::max<size_t>(em.size(), 64) * 2;
+    }
+    int err = TEBD_OK;
+    EigMat* dem = stage(c, em, &err);
+    if (err) return err;
+    size_t off = 0;
+    for (size_t t = 0; t < nc; ++t) {
+      tcut[t].mats = dem + off;
+      tcut[t].kmax_out = w.d_counts + off;
+      off += tcut[t].n;
+    }
+    ThrCut* dtc = stage(c, tcut, &err);
+    if (err) return err;
+    c->launches += eig_cut_counts(dtc, (int)nc, c->stream);
+    if (int r = ensure_back(c, em.size() / 2 + 8)) return r;
+    if (cudaMemcpyAsync(c->u1w->h_back, w.d_counts, sizeof(int) * em.size(), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+      return fail_cuda(c);
+    if (int r = sync(c)) return r;
+    const int* cnt = reinterpret_cast<const int*>(c->u1w->h_back);
+    for (size_t i = 0; i < order.size(); ++i) order[i]->kmax = std::max(0, std::min(order[i]->kmax, cnt[i]));
+    std::vector<Job> bj;
+    for (const Job& j : jobs)
+      if (j.B->kmax > 0) bj.push_back(j);
+    for (size_t g0 = 0; g0 < bj.size(); g0 += EIG_MAXP) {
       EigBatch eb{};
-      for (size_t j = g0; j < std::min(jobs.size(), g0 + EIG_MAXP); ++j) eb.a[eb.n++] = mat(jobs[j]);
+      for (size_t j = g0; j < std::min(bj.size(), g0 + EIG_MAXP); ++j) eb.a[eb.n++] = mat(bj[j]);
       c->launches += eig_bisect(eb, c->stream);
     }
   }
@@ -1736,7 +1789,8 @@ int u1_build_gate_blocks(tebd_ctx* c, const std::vector<std::complex<double>>& G
 
 size_t u1_workspace_bytes(const tebd_ctx* c) {
   if (!c->u1w) return 0;
-  size_t b = c->u1w->ring_bytes * c->u1w->ring.size() + c->u1w->stage_cap[0] + c->u1w->stage_cap[1];
+  size_t b = c->u1w->ring_bytes * c->u1w->ring.size() + c->u1w->ering_bytes * c->u1w->ering.size() +
+             c->u1w->stage_cap[0] + c->u1w->stage_cap[1];
   for (const U1Slot& s : c->u1w->slots) b += s.a1.cap + s.a2.cap;
   b += c->u1w->meas.cap;
   return b;
@@ -1750,6 +1804,7 @@ void u1_release(tebd_ctx* c) {
     if (s.a2.base) cudaFree(s.a2.base);
   }
   for (void* p : w.ring) cudaFree(p);
+  for (void* p : w.ering) cudaFree(p);
   if (w.meas.base) cudaFree(w.meas.base);
   for (int p = 0; p < 2; ++p) {
     for (auto& b : w.retired[p]) {
@@ -1761,6 +1816,7 @@ void u1_release(tebd_ctx* c) {
     if (w.ev[p]) cudaEventDestroy(w.ev[p]);
   }
   if (w.h_back) cudaFreeHost(w.h_back);
+  if (w.d_counts) cudaFree(w.d_counts);
   delete c->u1w;
   c->u1w = nullptr;
 }

@@ -57,6 +57,7 @@ class Request:
     eps_rel: float = 1e-12
     max_slots: int = 0
     deadline_s: Optional[float] = None  # cancelled if not finished this long after arrival
+    u1: bool = False                    # the particle-number-blocked form (option "u1")
 
 
 @dataclass
@@ -119,12 +120,15 @@ class Server:
         return ""
 
     def footprint(self, req: Request) -> float:
+        if req.u1:
+            return self.estimate_fn(req.L, req.n_max, req.chi_max, req.max_slots, self.precision, u1=True)
         return self.estimate_fn(req.L, req.n_max, req.chi_max, req.max_slots, self.precision)
 
     def _admit(self, req: Request, now: float) -> _Active:
+        kw = {"u1": True} if req.u1 else {}
         sim = self.sim_factory(req.L, req.n_max, req.chi_max, req.U, req.J, req.Jnnn, req.K, req.jc, req.dt,
                                w_cut=req.w_cut, eps_rel=req.eps_rel, precision=self.precision,
-                               stream=self.stream_ptr)
+                               stream=self.stream_ptr, **kw)
         try:
             if req.max_slots:
                 sim.set_option("max_slots", req.max_slots)
@@ -200,7 +204,12 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[0][0] - now)))
                 continue
             try:
-                self.step_fn([a.sim for a in active], 1)
+                # one batched step per form (the library batches simulations of one form together)
+                groups = {}
+                for a in active:
+                    groups.setdefault(a.req.u1, []).append(a.sim)
+                for sims in groups.values():
+                    self.step_fn(sims, 1)
             except Exception as e:  # the library fails every member of a failed batch
                 now = self.clock() - t0
                 for a in active:
