@@ -268,8 +268,8 @@ def dense_config2(stream, steps: int = 2, warmup: int = 1):
     return out
 
 
-SERVE_REQUESTS = 24      # config 5 streams 500; scaled to fit a bounded run
-SERVE_STEPS = (16, 8)    # steps of the headline-style / large requests (config 5: to t = 8 / t = 6)
+SERVE_REQUESTS = 16      # config 5 streams 500; scaled to fit a bounded run
+SERVE_STEPS = (12, 6)    # steps of the headline-style / large requests (config 5: to t = 8 / t = 6)
 SERVE_SLOTS = 4          # workspace slots per request (more requests fit the budget)
 SERVE_CONCURRENT = 6     # the HBM budget admits about this many headline-style requests at once
 
@@ -336,7 +336,7 @@ def served_measurement(stream_ptr):
             "one_at_a_time_fp64_dense_at_0.9": {**fifo_stats, "wall_s": fifo_s}}
 
 
-def batched_measurement(stream_ptr, steps: int = 2):
+def batched_measurement(stream_ptr, steps: int = 1):
     """Config 4: the 48 seeded simulations (L in 16..64, chi_max in 64..512, d = 4, seeded U, J_NNN,
     K; j_c = (L+1)/2), warm-started at chi_max: each from the charge-labelled synthetic saturated
     state of its chain at half filling (N = L/2), blocked form, mixed precision.  One

@@ -32,6 +32,14 @@ extern "C" {
 
 typedef struct tebd_ctx* tebd_handle;
 
+/* Source of the Gaussian test matrices of the randomized truncation (option
+ * "randomized"): called on the host once per truncated SVD with its index
+ * `call` (0, 1, 2, ... in the order of the updates: layer by layer, triples in
+ * increasing site order, cut 1 then cut 2 of each), its column count n and
+ * sketch size l; fills out[2 n l] with the n x l complex matrix (row-major,
+ * interleaved).  The random numbers are an input of the method. */
+typedef void (*tebd_test_matrix_fn)(long long call, int n, int l, double* out, void* ctx);
+
 enum {
   TEBD_OK = 0,
   TEBD_ERR_ARG = -1,           /* invalid argument (range, NULL, non-finite) */
@@ -65,6 +73,15 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
  *             2 = FP64-accurate throughout: the contractions too as exact-digit
  *             tensor-core products (the small gate product on FP64 CUDA cores)
  *   "max_slots" cap on triples processed concurrently (0 = automatic)
+ *   "randomized" 0 (default); 1: each truncated SVD of the dense form by the
+ *             randomized range finder the paper points to (Sec. V; Halko, Martinsson
+ *             and Tropp): a sketch of l = min(chi_max + "oversample", m, n) columns
+ *             from a caller-supplied test matrix (tebd_set_test_matrices), "power_iters"
+ *             re-orthonormalised power iterations, then the exact decomposition of the
+ *             l x n matrix Q^+ theta'; rule T with the tail from ||theta'||_F^2.  Every
+ *             product runs on the path's engine (exact-digit tensor-core products for
+ *             precision 1 and 2).  Dense form only (TEBD_ERR_ARG with "u1").
+ *   "oversample" p >= 0 (default 10), "power_iters" q >= 0 (default 2)
  *   "u1"      0 (default): dense local updates; 1: the particle-number blocked
  *             form of Sec. II B's U(1)-symmetric tensors.  Every gate conserves
  *             N, so each Schmidt vector carries a charge (tebd_set_charges) and
@@ -199,6 +216,13 @@ int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs,
  * blocked step without them returns TEBD_ERR_STATE.  Arrays are read before
  * the call returns. */
 int tebd_set_charges(tebd_handle h, const int* const* q_ptrs);
+
+/* Install the test-matrix source of the randomized truncation (fn NULL removes
+ * it) and restart its call index at 0.  ctx is passed to fn unchanged.  A
+ * randomized step without a source returns TEBD_ERR_STATE; a source that
+ * writes a non-finite value makes the step return TEBD_ERR_ARG.
+ * Infrastructure for the method's random input (no counterpart in the paper). */
+int tebd_set_test_matrices(tebd_handle h, tebd_test_matrix_fn fn, void* ctx);
 
 /* Copy the charges of bond k (0 <= k <= L) into q[chi_k] (host).  After every
  * blocked local update the new bonds are sorted by charge.  TEBD_ERR_STATE if

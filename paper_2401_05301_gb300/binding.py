@@ -20,6 +20,9 @@ _P_int = ctypes.POINTER(ctypes.c_int)
 _P_double = ctypes.POINTER(ctypes.c_double)
 _P_ll = ctypes.POINTER(ctypes.c_longlong)
 
+# void (*)(long long call, int n, int l, double* out, void* ctx): the randomized truncation's test matrices
+TEST_MATRIX_FN = ctypes.CFUNCTYPE(None, ctypes.c_longlong, _c_int, _c_int, _P_double, _c_void_p)
+
 # name -> (restype, argtypes); mirrors include/ptebd.h
 SIGNATURES = {
     "tebd_create": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
@@ -39,6 +42,7 @@ SIGNATURES = {
     "tebd_get_site": (_c_int, [_c_void_p, _c_int, _P_double, _P_double]),
     "tebd_set_state": (_c_int, [_c_void_p, _P_int, ctypes.POINTER(_P_double), ctypes.POINTER(_P_double)]),
     "tebd_set_charges": (_c_int, [_c_void_p, ctypes.POINTER(_P_int)]),
+    "tebd_set_test_matrices": (_c_int, [_c_void_p, TEST_MATRIX_FN, _c_void_p]),
     "tebd_get_charges": (_c_int, [_c_void_p, _c_int, _P_int]),
     "tebd_counters": (_c_int, [_c_void_p, _P_ll, _P_ll]),
     "tebd_profile": (_c_int, [_c_void_p, _c_int, _P_double, _P_ll, _P_double]),
@@ -211,6 +215,15 @@ class TEBD:
         qs = [np.ascontiguousarray(x, dtype=np.int32) for x in q]
         qp = (_P_int * len(qs))(*[x.ctypes.data_as(_P_int) for x in qs])
         _check(load().tebd_set_charges(self._h, qp), "tebd_set_charges")
+
+    def set_test_matrices(self, fn):
+        """Source of the randomized truncation's Gaussian test matrices: fn(call, n, l) returns the
+        n x l complex matrix of the call-th decomposition (an input of the method)."""
+        def cb(call, n, l, out, _ctx):
+            a = np.ascontiguousarray(fn(int(call), int(n), int(l)), dtype=np.complex128).reshape(n, l)
+            ctypes.memmove(out, a.ctypes.data, a.nbytes)
+        self._omega_cb = TEST_MATRIX_FN(cb) if fn is not None else TEST_MATRIX_FN()
+        _check(load().tebd_set_test_matrices(self._h, self._omega_cb, None), "tebd_set_test_matrices")
 
     def get_charges(self, k: int):
         chi = self.bond_dims()

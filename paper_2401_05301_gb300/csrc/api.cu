@@ -244,6 +244,8 @@ int alloc_workspace(tebd_ctx* c) {
     }
     c->slots.push_back(S);
   }
+  if (c->randomized)  // the range finder's row matrices live in per-slot arenas
+    if (int r = u1_alloc_slots(c, (int)c->slots.size())) return r;
   return ensure_pinned(c, (size_t)c->slots.size() * (c->kcap + 8) + 64);
 }
 
@@ -616,7 +618,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
         c->launches += g3.launch(s, tf32, c->d_status);
       }
     }
-    {
+    if (!c->randomized) {  // the randomized cut never forms the Gram matrix of theta'
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
       c->launches += mixed ? oz_gemm_launch(oz4, c->d_status, s) : g4.launch(s);
     }
@@ -630,6 +632,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       debug_dump(c, "H1", T.i, S.H, 2ull * T.m1 * T.m1);
     }
   }
+  if (c->randomized) {
+    if (int r = rand_cut(c, ts, false)) return r;
+  } else {
   if (int r = eigen_stage(c, ts, false)) return r;
   {  // Y1 = U1^+ (lam C)
     Gemm g5(true, OP_CJ, OP_N);
@@ -659,6 +664,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
     }
     if (int r = reorthonormalise(c, ts, false)) return r;
+  }
+  }
+  {
     // B_i = C V1 / ||s||;  Gram H2 = (lam' V1^+)(lam' V1^+)^+ viewed as (chi' d) x (d chr)
     Gemm g6(true, OP_N, OP_C), g7(true, OP_N, OP_C);
     std::vector<OzProb> oz7;
@@ -695,12 +703,15 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
         c->launches += g6.launch(s, tf32, c->d_status);
       }
     }
-    {
+    if (!c->randomized) {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
       c->launches += mixed ? oz_gemm_launch(oz7, c->d_status, s) : g7.launch(s);
     }
     if (int r = check_launch(c)) return r;
   }
+  if (c->randomized) {
+    if (int r = rand_cut(c, ts, true)) return r;
+  } else {
   if (int r = eigen_stage(c, ts, true)) return r;
   {  // Y2 = U2^+ (lam' V1^+)
     Gemm g8(true, OP_CJ, OP_N);
@@ -729,6 +740,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       c->launches += launch_gather_rows(ga.data(), (int)ga.size(), s);
     }
     if (int r = reorthonormalise(c, ts, true)) return r;
+  }
+  }
+  {
     // B_{i+1} = V1^+ V2 / ||s2||,  B_{i+2} = V2^+ (gathered above)
     Gemm g9(true, OP_N, OP_C);
     for (auto& T : ts) {
@@ -772,6 +786,9 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
   std::vector<Pending> rest;
   for (tebd_ctx* h : hs)
     for (int i = residue; i + 2 < h->L; i += 3) rest.push_back({h, i});
+  for (tebd_ctx* h : hs)  // a randomized simulation needs the workspace arenas (switched on late)
+    if (h->randomized)
+      if (int r = u1_alloc_slots(h, (int)h->slots.size())) return r;
   // Each chunk takes, in order, every pending triple whose simulation still has a free
   // workspace slot in this chunk, up to chunk_max triples; the triples of a layer are
   // disjoint, so any grouping gives the same (bitwise) result.
@@ -793,12 +810,15 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
       T.h = p.h;
       T.i = p.i;
       T.slot = taken;
+      T.call = p.h->rcall + 2 * ((p.i - residue) / 3);
       ts.push_back(T);
       if (k) ++*k; else used.push_back({p.h, 1});
     }
     if (int r = c->u1 ? update_chunk_u1(c, ts, tidx) : update_chunk(c, ts, tidx)) return r;
     rest.swap(later);
   }
+  for (tebd_ctx* h : hs)
+    for (int i = residue; i + 2 < h->L; i += 3) h->rcall += 2;
   return TEBD_OK;
 }
 
@@ -1011,8 +1031,19 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
       h->prof_launches[q] = 0;
       h->prof_work[q] = 0.0;
     }
+  } else if (k == "randomized") {
+    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if (value == 1.0 && h->u1) return TEBD_ERR_ARG;
+    h->randomized = (value == 1.0);
+  } else if (k == "oversample") {
+    if (value < 0 || value > 4096 || value != std::floor(value)) return TEBD_ERR_ARG;
+    h->oversample = (int)value;
+  } else if (k == "power_iters") {
+    if (value < 0 || value > 16 || value != std::floor(value)) return TEBD_ERR_ARG;
+    h->power_iters = (int)value;
   } else if (k == "u1") {
     if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if (value == 1.0 && h->randomized) return TEBD_ERR_ARG;
     if ((value == 1.0) != h->u1) {
       if (!h->slots.empty()) return TEBD_ERR_STATE;  // the workspace is laid out for one form
       h->u1 = (value == 1.0);
@@ -1084,6 +1115,14 @@ int tebd_set_charges(tebd_handle h, const int* const* q_ptrs) {
   if (q[0][0] != 0) return TEBD_ERR_ARG;
   h->q.swap(q);
   h->have_charges = true;
+  return TEBD_OK;
+}
+
+int tebd_set_test_matrices(tebd_handle h, tebd_test_matrix_fn fn, void* ctx) {
+  CHECK_HANDLE(h);
+  h->omega_fn = fn;
+  h->omega_ctx = ctx;
+  h->rcall = 0;
   return TEBD_OK;
 }
 

@@ -105,24 +105,40 @@ __global__ void k_trace(const __grid_constant__ EigBatch b) {
 // minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Sturm's theorem), with
 // a zero minor counted as a change.  Division-free: FP64 division is the
 // slowest operation on this part, and the minors are kept in range by exact
-// rescaling with 2^-500 / 2^500.
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x) {
+// rescaling with 2^-500 / 2^500.  ee[i] = e_i^2 (k_esq).  The loop is bound by
+// the FP64 pipe (two DFMA per clock per SM), so only the recurrence itself runs
+// there: the zero, sign and range tests read the IEEE-754 fields with integer
+// operations.  Rescaling by exact powers of two leaves every sign unchanged.
+__device__ __forceinline__ int sturm_count(const double* d, const double* ee, int m, double x) {
   const double big = 0x1p500, small = 0x1p-500;
   double pm = 1.0, p = d[0] - x;
   if (p == 0.0) p = -small;
-  int cnt = (p < 0.0);
+  long long bp = __double_as_longlong(p);
+  int cnt = (int)((unsigned long long)bp >> 63);
   for (int i = 1; i < m; ++i) {
-    const double ei = e[i - 1];
-    double pn = fma(d[i] - x, p, -(ei * ei) * pm);
-    if (pn == 0.0) pn = (p < 0.0) ? small : -small;
-    cnt += ((pn < 0.0) != (p < 0.0));
+    double pn = fma(d[i] - x, p, -(ee[i - 1] * pm));
+    long long bn = __double_as_longlong(pn);
+    if ((bn << 1) == 0) {  // a zero minor takes the sign opposite to the previous one
+      pn = (bp < 0) ? small : -small;
+      bn = __double_as_longlong(pn);
+    }
+    cnt += (int)((unsigned long long)(bn ^ bp) >> 63);
     pm = p;
     p = pn;
-    const double a = fabs(p);
-    if (a > big) { p *= small; pm *= small; }
-    else if (a < small) { p *= big; pm *= big; }
+    bp = bn;
+    const int ex = (int)((bn >> 52) & 0x7FF);
+    if (ex > 1023 + 500) { p *= small; pm *= small; bp = __double_as_longlong(p); }
+    else if (ex < 1023 - 500) { p *= big; pm *= big; bp = __double_as_longlong(p); }
   }
   return cnt;
+}
+
+// ee[i] = e_i^2 of every tridiagonal, for the Sturm counts, in the inverse-iteration
+// scratch (free until the eigenvectors are computed).
+__global__ void k_esq(const __grid_constant__ EigBatch b) {
+  const EigMat& M = b.a[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M.m; i += gridDim.x * blockDim.x)
+    M.work[i] = (i < M.m - 1) ? M.e[i] * M.e[i] : 0.0;
 }
 
 __device__ void gershgorin(const double* d, const double* e, int m, double* sh, double& gl, double& gu) {
@@ -163,7 +179,7 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
     const bool conv = !(hi - lo > atol);
     if (__all_sync(0xffffffffu, conv || !active)) break;
     const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / 9.0);
-    const bool above = active && !conv && sturm_count(M.d, M.e, m, x) > target;  // eigenvalue below x
+    const bool above = active && !conv && sturm_count(M.d, M.work, m, x) > target;  // eigenvalue below x
     const unsigned gb = (__ballot_sync(0xffffffffu, above) >> (8 * g)) & 0xFFu;
     const int l0 = gb ? (__ffs(gb) - 1) : 8;  // first point above the eigenvalue (8: none)
     const double xa = __shfl_sync(0xffffffffu, x, 8 * g + (l0 > 0 ? l0 - 1 : 0));
@@ -184,7 +200,7 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
 // multisection on the summed Sturm counts: P points per matrix per iteration, each
 // iteration shrinking the bracket by P + 1, then writes per matrix the number of
 // its eigenvalues at or above the bracket's lower end (capped by kmax).
-__device__ __forceinline__ int count_at_or_above(const EigMat& M, double x) { return M.m - sturm_count(M.d, M.e, M.m, x); }
+__device__ __forceinline__ int count_at_or_above(const EigMat& M, double x) { return M.m - sturm_count(M.d, M.work, M.m, x); }
 
 __global__ void __launch_bounds__(1024) k_cut_counts(const ThrCut* __restrict__ cuts) {
   const ThrCut C = cuts[blockIdx.x];
@@ -1056,7 +1072,8 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
     }
     launches += mixed ? oz_gemm_launch(oz, status, s) : g.launch(s);
   }
-  return launches;
+  k_esq<<<dim3(std::max(1, std::min(64, (mm + 255) / 256)), b.n), 256, 0, s>>>(b);
+  return launches + 1;
 }
 
 size_t eig_panel_doubles2(int m) {

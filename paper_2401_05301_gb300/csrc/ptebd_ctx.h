@@ -33,6 +33,7 @@ struct Triple {
   int chl, c1, c2, chr;
   int m1, n1, K1, chi1, m2, n2, K2, chi2;
   double norm1, norm2, w1, w2;
+  long long call;  // randomized truncation: index of cut 1's test matrix (cut 2: call + 1)
 };
 
 struct U1Work;  // workspace of the blocked form (u1.cu)
@@ -79,6 +80,12 @@ struct tebd_ctx {
   double2* Gblk = nullptr;  // gates restricted to each total-occupation block (u1.cu layout)
   size_t Gblk_n = 0;        // complex elements of Gblk
   ptebd::U1Work* u1w = nullptr;
+  // randomized range finder for the truncated SVDs (option "randomized", dense form)
+  bool randomized = false;
+  int oversample = 10, power_iters = 2;
+  tebd_test_matrix_fn omega_fn = nullptr;
+  void* omega_ctx = nullptr;
+  long long rcall = 0;  // decompositions so far (the test-matrix call index)
   // optional per-class timing (CUDA events on the handle's stream)
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[TEBD_PROF_NCLASS];
@@ -159,5 +166,8 @@ int u1_alloc_slots(tebd_ctx* c, int nslots);
 // Correlators <b+_k b_{k+1}> of every bond (out: device, L-1 complex) from the charge
 // blocks of the canonical form; needs the handle's charges.
 int u1_correlators(tebd_ctx* h, double2* out);
+// Dense form: cut 1 (second = false: theta' = lam C into V1^+) or cut 2 (R into B_{i+2}) of
+// every triple by the randomized range finder; sets chi, norm and w of the triples.
+int rand_cut(tebd_ctx* c, std::vector<Triple>& ts, bool second);
 
 }  // namespace ptebd

@@ -635,6 +635,7 @@ struct Cut {
   int chi_cap = 1;
   double w_cut = 0.0, eps_rel = 1e-12;  // the owning simulation's options
   double total = 0.0;
+  double total_fixed = -1.0;  // if >= 0: ||M||_F^2 of a partial decomposition (rule T's tail)
   size_t oS, oRow, oCnt, oChi, oNorm, oW;  // truncation outputs
   int chi = 1;
   double norm = 1.0, w = 0.0;
@@ -872,6 +873,8 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
       cuts[j.t]->total += j.B->trace;
       o += j.B->kmax + 1;
     }
+    for (auto& cut : cuts)
+      if (cut->total_fixed >= 0.0) cut->total = cut->total_fixed;
     o = 0;
     for (size_t q = 0; q < jobs.size(); ++q) {
       Job& j = jobs[q];
@@ -1628,6 +1631,261 @@ int update_chunk_u1(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   if (int r = stage_begin_chunk(c)) return r;
   const int r = update_chunk_u1_body(c, ts, tidx);
   // the staging buffer of this chunk is reusable once the work issued so far has run
+  const int re = stage_end_chunk(c);
+  return r != TEBD_OK ? r : re;
+}
+
+namespace {
+
+// ---- randomized range finder for the dense form (the cheaper SVD of Sec. V) -------------
+
+__global__ void k_fill(double* __restrict__ x, size_t n, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+// out[t] = ||M_t||_F^2 with M_t[r][:] = lam_t[r / d] X_t[r][:] (m_t x n_t, row-major)
+struct FrobArgs {
+  const double2* X;
+  const double* lam;
+  int m, n, d;
+  double* out;
+};
+__global__ void k_frob(const FrobArgs* __restrict__ fa) {
+  const FrobArgs F = fa[blockIdx.x];
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < (long long)F.m * F.n; e += blockDim.x) {
+    const int r = (int)(e / F.n);
+    const double l = F.lam[r / F.d];
+    const double2 v = F.X[e];
+    acc = fma(l * l, fma(v.x, v.x, v.y * v.y), acc);
+  }
+  acc = warp_sum_d(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *F.out = t;
+  }
+}
+
+// One cut of one block for a row matrix P (rows x cols) already in the arena's layout:
+// every direction kept (an orthonormal basis of the row space), or rule T (final).
+void one_block_cut(Cut& cut, int rows, int cols, int chi_cap, double w_cut, double eps_rel, Bump& bp) {
+  cut = Cut{};
+  CutBlk B{};
+  B.b = rows;
+  B.n = cols;
+  B.kmax = std::min({rows, cols, chi_cap});
+  cut.blk.push_back(B);
+  cut.chi_cap = chi_cap;
+  cut.w_cut = w_cut;
+  cut.eps_rel = eps_rel;
+  layout_cut(cut, bp);
+}
+
+// The row matrix of a triple's cut: M[r][:] = lam[r / d] X[r][:], m x n (dense form).
+struct RandIn {
+  const double2* X;
+  const double* lam;
+  int m, n, d;
+};
+
+// Products with M on the engine of the path: C (rows x N) = A op(M) with op(M) = M (then
+// the reduction runs over the rows of M, scaled by lam) or M^+ (then the columns of the
+// result are the rows of M, scaled by lam); A is rows x K (or Omega^+ when omega).
+void prod_with_M(tebd_ctx* c, Gemm& gN, Gemm& gC, std::vector<OzProb>& oz, const RandIn& in, const double2* A,
+                 int rows, bool adjoint, bool omega, double2* C) {
+  const bool mixed = c->precision >= 1;
+  if (!adjoint) {  // C = A M: A rows x m, C rows x n
+    if (mixed) {
+      OzProb q{};
+      q.a = OzOperand{A, in.m, 1, in.lam, in.d, 0};
+      q.b = OzOperand{in.X, 1, in.n, nullptr, 1, 0};
+      q.M = rows; q.N = in.n; q.K = in.m; q.C = C; q.ldc = in.n; q.alpha = 1.0; q.row_div = q.col_div = 1;
+      oz.push_back(q);
+    } else {
+      GemmProb& p = gN.add(rows, in.n, in.m, A, in.m, in.X, in.n, C, in.n);
+      p.s_red = in.lam;
+      p.red_div = in.d;
+    }
+  } else {  // C = A M^+: A rows x n (or Omega^+ with Omega n x rows), C rows x m
+    if (mixed) {
+      OzProb q{};
+      q.a = omega ? OzOperand{A, 1, rows, nullptr, 1, 1} : OzOperand{A, in.n, 1, nullptr, 1, 0};
+      q.b = OzOperand{in.X, in.n, 1, nullptr, 1, 1};
+      q.M = rows; q.N = in.m; q.K = in.n; q.C = C; q.ldc = in.m; q.alpha = 1.0;
+      q.s_col = in.lam; q.row_div = 1; q.col_div = in.d;
+      oz.push_back(q);
+    } else {  // omega: gC computes Omega^+ M^+ (both operands conjugate-transposed); else gN is (N, C)
+      GemmProb& p = (omega ? gC : gN).add(rows, in.m, in.n, A, omega ? rows : in.n, in.X, in.n, C, in.m);
+      p.s_col = in.lam;
+      p.col_div = in.d;
+    }
+  }
+}
+
+int run_M_prods(tebd_ctx* c, Gemm& gN, Gemm& gC, std::vector<OzProb>& oz, double w) {
+  ProfScope ps(c, TEBD_PROF_PROJECT, w);
+  if (c->precision >= 1) {
+    size_t need = 0;
+    for (const OzProb& q : oz) need = std::max(need, oz_workspace_bytes(q.M, q.N, q.K, false));
+    if (int r = ensure_ring(c, need)) return r;
+    for (size_t j = 0; j < oz.size(); ++j) oz[j].ws = c->u1w->ring[j % OZ_MAXP];
+    c->launches += oz_gemm_launch(oz, c->d_status, c->stream);
+  } else {
+    c->launches += gN.launch(c->stream);
+    c->launches += gC.launch(c->stream);
+  }
+  return check_launch(c);
+}
+
+}  // namespace
+
+namespace {
+
+int rand_cut_body(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
+  const size_t nt = ts.size();
+  std::vector<RandIn> in(nt);
+  std::vector<int> ell(nt);
+  std::vector<U1Slot*> sl(nt);
+  for (size_t t = 0; t < nt; ++t) {
+    Triple& T = ts[t];
+    tebd_ctx* o = T.h;
+    const Slot& S = o->slots[T.slot];
+    if (!o->omega_fn) return TEBD_ERR_STATE;
+    in[t] = second ? RandIn{S.V1h, o->lam[T.i + 1], T.m2, T.n2, o->d} : RandIn{S.Cb, o->lam[T.i], T.m1, T.n1, o->d};
+    ell[t] = std::min({o->chi_max + o->oversample, in[t].m, in[t].n});
+    sl[t] = &o->u1w->slots[T.slot];
+  }
+  // Omega of each decomposition from the caller (an input, never drawn here) into arena a2,
+  // and ||M||_F^2 beside it
+  std::vector<FrobArgs> fa(nt);
+  std::vector<double> host;
+  for (size_t t = 0; t < nt; ++t) {
+    const size_t ob = align256(16 * (size_t)in[t].n * ell[t]);
+    if (int r = ensure_arena(c, sl[t]->a2, ob + 256)) return r;
+  }
+  for (size_t t = 0; t < nt; ++t) {
+    Triple& T = ts[t];
+    host.assign(2 * (size_t)in[t].n * ell[t], 0.0);
+    T.h->omega_fn(T.call + (second ? 1 : 0), in[t].n, ell[t], host.data(), T.h->omega_ctx);
+    for (double x : host)
+      if (!is_fin(x)) return TEBD_ERR_ARG;
+    // a pageable copy is staged before the call returns, so host can be refilled at once
+    if (cudaMemcpy(sl[t]->a2.base, host.data(), 8 * host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail_cuda(c);
+    fa[t] = FrobArgs{in[t].X, in[t].lam, in[t].m, in[t].n, in[t].d,
+                     reinterpret_cast<double*>(sl[t]->a2.base + align256(16 * (size_t)in[t].n * ell[t]))};
+  }
+  {
+    int err = TEBD_OK;
+    FrobArgs* dfa = stage(c, fa, &err);
+    if (err) return err;
+    k_frob<<<(unsigned)nt, 256, 0, c->stream>>>(dfa);
+    c->launches += 1;
+    if (int r = check_launch(c)) return r;
+  }
+  if (int r = ensure_back(c, nt + 2)) return r;
+  for (size_t t = 0; t < nt; ++t) cudaMemcpyAsync(c->u1w->h_back + t, fa[t].out, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (int r = sync(c)) return r;
+  std::vector<double> frob(nt);
+  for (size_t t = 0; t < nt; ++t) {
+    frob[t] = c->u1w->h_back[t];
+    if (!is_fin(frob[t]) || !(frob[t] > 0.0)) {
+      c->sticky = TEBD_ERR_NONFINITE;
+      return TEBD_ERR_NONFINITE;
+    }
+  }
+  // Yh = Omega^+ M^+ (l x m); q times Zh = Q M (r x n), Yh = Z M^+ (r x m); C = Q M (r x n).
+  // Every intermediate row matrix is replaced by an orthonormal basis of its row space (a
+  // one-block cut that keeps every direction above the Gram floor); the last, C, is cut by
+  // rule T with the tail from ||M||_F^2.  The steps alternate between the slot's arenas.
+  const int nsteps = 2 + 2 * std::max(0, c->power_iters);
+  std::vector<Cut> prev(nt), cur(nt);
+  std::vector<int> rows(ell);
+  std::vector<char*> pbase(nt);
+  for (int stp = 0; stp < nsteps; ++stp) {
+    const bool final_step = (stp == nsteps - 1);
+    const bool adj = (stp % 2 == 0);  // the Yh steps multiply by M^+
+    std::vector<Cut*> cp(nt);
+    std::vector<char*> bases(nt);
+    std::vector<double*> lo(nt);
+    std::vector<size_t> lam_off(nt);
+    for (size_t t = 0; t < nt; ++t) {
+      Triple& T = ts[t];
+      tebd_ctx* o = T.h;
+      const int cols = adj ? in[t].m : in[t].n;
+      Bump bp;
+      if (final_step)
+        one_block_cut(cur[t], rows[t], cols, std::min(o->chi_max, o->cap[T.i + (second ? 2 : 1)]), o->w_cut,
+                      o->eps_rel, bp);
+      else
+        one_block_cut(cur[t], rows[t], cols, std::min(rows[t], cols), 0.0, 0.0, bp);
+      cur[t].total_fixed = final_step ? frob[t] : -1.0;
+      lam_off[t] = bp.take(8 * (size_t)rows[t]);
+      U1Arena& dst = (stp % 2 == 0) ? sl[t]->a1 : sl[t]->a2;
+      if (int r = ensure_arena(c, dst, bp.used)) return r;
+      bases[t] = dst.base;
+      cp[t] = &cur[t];
+      lo[t] = final_step ? o->lam[T.i + (second ? 2 : 1)] : at<double>(dst.base, lam_off[t]);
+    }
+    // the row matrix of this step from the previous basis (or Omega)
+    {
+      Gemm gN(true, OP_N, OP_N), gC(true, OP_C, OP_C), gNC(true, OP_N, OP_C);
+      std::vector<OzProb> oz;
+      double w = 0.0;
+      for (size_t t = 0; t < nt; ++t) {
+        const CutBlk& B = cur[t].blk[0];
+        double2* P = at<double2>(bases[t], B.oP);
+        if (stp == 0) {
+          prod_with_M(c, gN, gC, oz, in[t], reinterpret_cast<const double2*>(sl[t]->a2.base), rows[t], true, true, P);
+        } else {
+          const CutBlk& Bp = prev[t].blk[0];
+          const double2* Wp = at<double2>(pbase[t], Bp.oW);
+          prod_with_M(c, adj ? gNC : gN, gC, oz, in[t], Wp, rows[t], adj, false, P);
+        }
+        w += 8.0 * (double)rows[t] * in[t].m * in[t].n;
+        k_fill<<<(rows[t] + 255) / 256, 256, 0, c->stream>>>(at<double>(bases[t], B.oLam), (size_t)rows[t], 1.0);
+        c->launches += 1;
+      }
+      if (int r = run_M_prods(c, gN, gC, oz, w)) return r;
+      c->launches += gNC.launch(c->stream);
+      if (int r = check_launch(c)) return r;
+    }
+    if (int r = decompose(c, cp, bases, lo)) return r;
+    if (int r = kept_vectors(c, cp, bases)) return r;
+    for (size_t t = 0; t < nt; ++t) {
+      rows[t] = cur[t].chi;
+      pbase[t] = bases[t];
+    }
+    std::swap(prev, cur);
+  }
+  // the kept right vectors into the site workspace (cut 1: V1^+) or tensor (cut 2: B_{i+2})
+  for (size_t t = 0; t < nt; ++t) {
+    Triple& T = ts[t];
+    tebd_ctx* o = T.h;
+    const Cut& F = prev[t];
+    const CutBlk& B = F.blk[0];
+    double2* dst = second ? o->B[T.i + 2] : o->slots[T.slot].V1h;
+    if (cudaMemcpyAsync(dst, at<double2>(pbase[t], B.oW), 16 * (size_t)F.chi * B.n, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      return fail_cuda(c);
+    if (second) { T.chi2 = F.chi; T.norm2 = F.norm; T.w2 = F.w; }
+    else { T.chi1 = F.chi; T.norm1 = F.norm; T.w1 = F.w; }
+  }
+  return check_launch(c);
+}
+
+}  // namespace
+
+int rand_cut(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
+  if (!c->u1w) return TEBD_ERR_STATE;
+  for (const Triple& T : ts)
+    if (!T.h->u1w || (int)T.h->u1w->slots.size() <= T.slot) return TEBD_ERR_STATE;
+  if (int r = stage_begin_chunk(c)) return r;
+  const int r = rand_cut_body(c, ts, second);
   const int re = stage_end_chunk(c);
   return r != TEBD_OK ? r : re;
 }
