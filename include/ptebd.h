@@ -62,6 +62,27 @@ enum {
 int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K,
                 double j_c, double dt, tebd_handle* out);
 
+/* Create a simulation of eq. (1) on L physical sites in the paper's own scheme
+ * (Sec. II B): every two neighbouring sites form one super site of local dimension
+ * d_e = (n_max + 1)^2 (basis sigma = s_a (n_max + 1) + s_b, s_a the left site), an
+ * odd chain first gets one extra empty site at its end, so the MPS has
+ * L_e = ceil(L / 2) super sites and nearest-neighbour two-site gates of dimension
+ * d_e^2.  The super bond (k, k+1) holds the NN and both NNN hops between the two
+ * super sites; each term inside a super site (its hop and on-site terms) is shared
+ * equally among the one or two super bonds that contain it, so the bond terms sum
+ * to eq. (1) on the padded chain.  Gates exp(-i h_k tau) are built per occupation
+ * block (every term conserves N).  A step is odd bonds dt/2, even bonds dt, odd
+ * bonds dt/2, one SVD per gate, the B-form two-site update.
+ *   L >= 3, 1 <= n_max <= 4 (d_e <= 25), chi_max >= 1; other arguments as tebd_create.
+ * On the handle: tebd_init_product takes the L physical occupations (the padded
+ * site starts empty); tebd_set_state, tebd_get_site and tebd_bond_dims see the
+ * L_e super sites; tebd_measure writes 2 L_e densities and 2 L_e - 1 currents of
+ * the padded physical chain; tebd_layer takes residue 0 (odd bonds k = 1, 3, ...)
+ * or 1 (even bonds).  "u1", "randomized" and trotter_order 4 are refused
+ * (TEBD_ERR_ARG); a batch must not mix super-site and three-site handles. */
+int tebd_create_supersite(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K,
+                          double j_c, double dt, tebd_handle* out);
+
 /* Set a numerical option; valid before or between steps.
  *   "w_cut"   discarded-weight cut: keep the fewest values whose discarded
  *             weight sum_{i>chi'} p_i <= w_cut, p_i = s_i^2 / sum s^2  (default 0)
@@ -278,6 +299,15 @@ int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K,
  * below 1e-32 of the Frobenius norm within max_sweeps.  Host only. */
 int tebd_gate_host_sweeps(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
                           int j, double tau, int max_sweeps, double* out);
+
+/* Host-only helper (no GPU needed): the FP64 gate exp(-i h_k tau) of super bond k
+ * (1-based, 1 <= k <= L_e - 1, L_e = ceil(L / 2)) of the super-site scheme
+ * (tebd_create_supersite) as a d^4 x d^4 row-major complex matrix, d = n_max + 1,
+ * over the physical sites (2k-1, 2k, 2k+1, 2k+2) with the last fastest, written
+ * interleaved into out[2 d^8]; 1 <= n_max <= 4.  Exponentiated per block of fixed
+ * boson number with the library's Hermitian Jacobi eigen-solver. */
+int tebd_gate_host_supersite(int L, int n_max, double U, double J, double J_NNN, double K, double j_c,
+                             int k, double tau, double* out);
 
 /* The complex contraction used by the local update of Sec. II B (theta, gate,
  * rebuild), exposed for direct use and testing: C = alpha * A * op(B) on device buffers (interleaved complex doubles,

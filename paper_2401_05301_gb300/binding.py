@@ -27,6 +27,8 @@ TEST_MATRIX_FN = ctypes.CFUNCTYPE(None, ctypes.c_longlong, _c_int, _c_int, _P_do
 SIGNATURES = {
     "tebd_create": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
                              _c_double, ctypes.POINTER(_c_void_p)]),
+    "tebd_create_supersite": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double,
+                                       _c_double, _c_double, ctypes.POINTER(_c_void_p)]),
     "tebd_set_option": (_c_int, [_c_void_p, ctypes.c_char_p, _c_double]),
     "tebd_set_stream": (_c_int, [_c_void_p, _c_void_p]),
     "tebd_init_product": (_c_int, [_c_void_p, _P_int]),
@@ -56,6 +58,8 @@ SIGNATURES = {
                                 _c_double, _P_double]),
     "tebd_gate_host_sweeps": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
                                        _c_int, _c_double, _c_int, _P_double]),
+    "tebd_gate_host_supersite": (_c_int, [_c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
+                                          _c_int, _c_double, _P_double]),
 }
 
 _LIB = None
@@ -129,16 +133,28 @@ def gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, max_sweeps) -> np.ndar
     return out.view(np.complex128).reshape(d ** 3, d ** 3)
 
 
+def gate_host_supersite(L, n_max, U, J, Jnnn, K, jc, k, tau) -> np.ndarray:
+    """The library's host-built gate exp(-i h_k tau) of super bond k, d^4 x d^4 complex."""
+    d = n_max + 1
+    out = np.empty(2 * d ** 8, dtype=np.float64)
+    _check(load().tebd_gate_host_supersite(L, n_max, U, J, Jnnn, K, jc, k, tau, _dptr(out)),
+           "tebd_gate_host_supersite")
+    return out.view(np.complex128).reshape(d ** 4, d ** 4)
+
+
 class TEBD:
     """One simulation handle (see include/ptebd.h for every call's contract)."""
 
     def __init__(self, L, n_max, chi_max, U, J, Jnnn, K, jc, dt, w_cut=None, eps_rel=None, precision=None,
                  stream=None, u1=None):
-        lib = load()
         h = _c_void_p()
-        _check(lib.tebd_create(L, n_max, chi_max, U, J, Jnnn, K, jc, dt, ctypes.byref(h)), "tebd_create")
+        _check(load().tebd_create(L, n_max, chi_max, U, J, Jnnn, K, jc, dt, ctypes.byref(h)), "tebd_create")
         self._h = h
         self.L, self.d, self.J = L, n_max + 1, J
+        self.n_meas = L
+        self._options(w_cut, eps_rel, precision, stream, u1)
+
+    def _options(self, w_cut, eps_rel, precision, stream, u1):
         if w_cut is not None:
             self.set_option("w_cut", w_cut)
         if eps_rel is not None:
@@ -167,8 +183,8 @@ class TEBD:
         _check(load().tebd_layer(self._h, int(residue), int(bool(full))), "tebd_layer")
 
     def measure(self):
-        n = np.empty(self.L)
-        cur = np.empty(self.L - 1)
+        n = np.empty(self.n_meas)
+        cur = np.empty(self.n_meas - 1)
         _check(load().tebd_measure(self._h, _dptr(n), _dptr(cur)), "tebd_measure")
         return n, cur
 
@@ -259,3 +275,21 @@ class TEBD:
             self.close()
         except Exception:
             pass
+
+
+class SuperSiteTEBD(TEBD):
+    """A handle of the super-site scheme (tebd_create_supersite): L physical sites as
+    ceil(L / 2) super sites of local dimension (n_max + 1)^2.  L, d, get_site and
+    bond_dims refer to the super sites; measure() returns the padded physical chain
+    (2 ceil(L / 2) densities and one current fewer)."""
+
+    def __init__(self, L, n_max, chi_max, U, J, Jnnn, K, jc, dt, w_cut=None, eps_rel=None, precision=None,
+                 stream=None):
+        h = _c_void_p()
+        _check(load().tebd_create_supersite(L, n_max, chi_max, U, J, Jnnn, K, jc, dt, ctypes.byref(h)),
+               "tebd_create_supersite")
+        self._h = h
+        self.L_phys = L
+        self.L, self.d, self.J = (L + L % 2) // 2, (n_max + 1) ** 2, J
+        self.n_meas = 2 * self.L
+        self._options(w_cut, eps_rel, precision, stream, None)

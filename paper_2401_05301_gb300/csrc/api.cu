@@ -92,22 +92,26 @@ namespace {
 // bench's device_bytes) and rounded up.
 constexpr double U1_ARENA_FRACTION = 0.5;
 
-int max_triples_per_layer(int L) {
+int max_triples_per_layer(int L, bool ss = false) {
+  const int stride = ss ? 2 : 3, span = ss ? 1 : 2;  // super sites: NN bonds, two layers
   int best = 0;
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < stride; ++r) {
     int n = 0;
-    for (int i = r; i + 2 < L; i += 3) ++n;
+    for (int i = r; i + span < L; i += stride) ++n;
     best = std::max(best, n);
   }
   return best;
 }
 
+// Local updates per time index: triples (L - 2) or super bonds (L - 1).
+int gate_sites(const tebd_ctx* c) { return c->ss ? c->L - 1 : c->L - 2; }
+
 // Device bytes of one workspace slot (one triple in flight) for bond capacity
 // capmax, local dimension d and bond cap chi_max.
 // Digit workspace of the mixed path: the largest of the Gram H1 (m x m over n1),
 // projection Y1 (K x n1 over m) and projection Y2 (K x m over m) products.
-double oz_slot_bytes(long long capmax, long long d, long long chi_max) {
-  const long long mm = capmax * d, n1max = d * d * capmax, kc = std::min<long long>(mm, chi_max);
+double oz_slot_bytes(long long capmax, long long d, long long chi_max, bool two_site = false) {
+  const long long mm = capmax * d, n1max = (two_site ? d : d * d) * capmax, kc = std::min<long long>(mm, chi_max);
   return (double)std::max({oz_workspace_bytes((int)mm, (int)mm, (int)n1max, true),
                            oz_workspace_bytes((int)kc, (int)n1max, (int)mm, false),
                            oz_workspace_bytes((int)kc, (int)mm, (int)mm, false),
@@ -118,13 +122,14 @@ double oz_slot_bytes(long long capmax, long long d, long long chi_max) {
                            oz_workspace_bytes((int)mm, (int)kc, (int)mm, false)});
 }
 
-double slot_bytes_for(long long capmax, long long d, long long chi_max, int precision) {
-  const long long D = d * d * d, mm = capmax * d, n1max = d * d * capmax;
+double slot_bytes_for(long long capmax, long long d, long long chi_max, int precision, bool two_site = false) {
+  const long long D = two_site ? d * d : d * d * d, mm = capmax * d, n1max = (two_site ? d : d * d) * capmax;
   const long long kc = std::min<long long>(mm, chi_max);
-  return 16.0 * (capmax * d * d * capmax + 2.0 * capmax * D * capmax + mm * mm + capmax * n1max + 3.0 * mm +
-                 EIG_PARTS + kc * mm) +
+  // two sites: the projection and V^+ rows (Th, V1h) are at most kc x n1
+  const double th_v = two_site ? 2.0 * kc * n1max : capmax * D * capmax + capmax * n1max;
+  return 16.0 * (capmax * d * d * capmax + capmax * D * capmax + th_v + mm * mm + 3.0 * mm + EIG_PARTS + kc * mm) +
          8.0 * (4.0 * mm + 4 + 7.0 * mm * kc + kc * kc) + 4.0 * (mm + 1) + 16.0 * eig_panel_doubles2((int)mm) +
-         (precision >= 1 ? oz_slot_bytes(capmax, d, chi_max) : 0.0);
+         (precision >= 1 ? oz_slot_bytes(capmax, d, chi_max, two_site) : 0.0);
 }
 
 std::vector<int> bond_caps(int L, int d, int chi_max) {
@@ -147,6 +152,10 @@ std::vector<double> gate_taus(const tebd_ctx* c) {
 // five times (order 4).  Adjacent half-step layers are never merged.
 std::vector<std::pair<int, int>> step_layers(const tebd_ctx* c) {
   std::vector<std::pair<int, int>> out;
+  if (c->ss) {  // super sites: odd bonds dt/2, even bonds dt, odd bonds dt/2 (Sec. II B)
+    out = {{0, 0}, {1, 1}, {0, 0}};
+    return out;
+  }
   auto s2 = [&](int half, int full) {
     const std::pair<int, int> l[5] = {{0, half}, {1, half}, {2, full}, {1, half}, {0, half}};
     out.insert(out.end(), l, l + 5);
@@ -161,22 +170,26 @@ std::vector<std::pair<int, int>> step_layers(const tebd_ctx* c) {
 
 // Build every gate of the table on the host (exact exponentiation) and upload it.
 int build_gates(tebd_ctx* c) {
-  const size_t DD = (size_t)c->D * c->D, L2 = (size_t)c->L - 2;
+  const size_t DD = (size_t)c->D * c->D, L2 = (size_t)gate_sites(c);
   const std::vector<double> taus = gate_taus(c);
   double2* G = dalloc<double2>(c, taus.size() * L2 * DD);
   if (!G) return TEBD_ERR_OOM;
   std::vector<std::complex<double>> Gall(taus.size() * L2 * DD), Gj;
   for (size_t t = 0; t < taus.size(); ++t)
-    for (int j = 1; j <= c->L - 2; ++j) {
-      if (!build_gate(c->L, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t], Gj, c->jacobi_sweeps))
-        return TEBD_ERR_NOT_CONVERGED;
+    for (int j = 1; j <= (int)L2; ++j) {
+      const bool ok = c->ss ? build_gate_supersite(c->L_phys, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t],
+                                                   Gj, c->jacobi_sweeps)
+                            : build_gate(c->L, c->n_max, c->U, c->J, c->Jnnn, c->K, c->jc, j, taus[t], Gj,
+                                         c->jacobi_sweeps);
+      if (!ok) return TEBD_ERR_NOT_CONVERGED;
       std::copy(Gj.begin(), Gj.end(), Gall.begin() + (t * L2 + (j - 1)) * DD);
     }
   if (cudaMemcpy(G, Gall.data(), Gall.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();
     return TEBD_ERR_CUDA;
   }
-  if (int r = u1_build_gate_blocks(c, Gall, taus.size() * L2)) return r;
+  if (!c->ss)
+    if (int r = u1_build_gate_blocks(c, Gall, taus.size() * L2)) return r;
   if (c->G) {  // replace the previous table
     for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
       if (*it == c->G) { c->allocs.erase(it); break; }
@@ -191,7 +204,7 @@ int build_gates(tebd_ctx* c) {
 int alloc_workspace(tebd_ctx* c) {
   if (!c->slots.empty()) return TEBD_OK;
   if (c->u1) {  // the blocked form: slots hold only arenas that grow with the blocks
-    int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
+    int want = std::min(max_triples_per_layer(c->L, c->ss), MAX_SLOTS);
     if (c->max_slots > 0) want = std::min(want, c->max_slots);
     if (int r = u1_alloc_slots(c, want)) return r;
     c->slots.assign(want, Slot{});
@@ -202,24 +215,24 @@ int alloc_workspace(tebd_ctx* c) {
   for (int v : c->cap) capmax = std::max<long long>(capmax, v);
   c->capmax = capmax;
   c->mmax = capmax * d;
-  c->n1max = d * d * capmax;
+  c->n1max = (c->ss ? d : d * d) * capmax;
   c->kcap = std::min<long long>(c->mmax, c->chi_max);
   if (c->mmax > 12288) return TEBD_ERR_ARG;  // the reduction's partial sums are sized for m <= 12288
   const long long D = c->D, mm = c->mmax, kc = c->kcap;
-  const double slot_bytes = slot_bytes_for(capmax, d, c->chi_max, c->precision);
+  const double slot_bytes = slot_bytes_for(capmax, d, c->chi_max, c->precision, c->ss);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  int want = std::min(max_triples_per_layer(c->L), MAX_SLOTS);
+  int want = std::min(max_triples_per_layer(c->L, c->ss), MAX_SLOTS);
   if (c->max_slots > 0) want = std::min(want, c->max_slots);
   const int budget = (int)std::max(1.0, std::floor(0.8 * (double)free_b / slot_bytes));
   const int nslots = std::max(1, std::min(want, budget));
   for (int s = 0; s < nslots; ++s) {
     Slot S{};
     S.X = dalloc<double2>(c, capmax * d * d * capmax);
-    S.Th = dalloc<double2>(c, capmax * D * capmax);
+    S.Th = dalloc<double2>(c, c->ss ? kc * c->n1max : capmax * D * capmax);
     S.Cb = dalloc<double2>(c, capmax * D * capmax);
     S.H = dalloc<double2>(c, mm * mm);
-    S.V1h = dalloc<double2>(c, capmax * c->n1max);
+    S.V1h = dalloc<double2>(c, (c->ss ? kc : capmax) * c->n1max);
     S.tau = dalloc<double2>(c, mm);
     S.part = dalloc<double2>(c, EIG_PARTS);
     S.p = dalloc<double2>(c, mm);
@@ -236,7 +249,7 @@ int alloc_workspace(tebd_ctx* c) {
     S.perm = dalloc<int>(c, mm);
     S.chi = dalloc<int>(c, 1);
     S.pan = dalloc<double2>(c, eig_panel_doubles2((int)mm));
-    if (c->precision >= 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max));
+    if (c->precision >= 1) S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(capmax, d, c->chi_max, c->ss));
     if ((c->precision >= 1 && !S.oz) || !S.pan || !S.X || !S.Th || !S.Cb || !S.H || !S.V1h || !S.tau || !S.part || !S.p || !S.U || !S.d || !S.e ||
         !S.evals || !S.Z || !S.Z2 || !S.S || !S.work || !S.s_sorted || !S.scal || !S.perm || !S.chi) {
       if (s == 0) return TEBD_ERR_OOM;
@@ -252,7 +265,7 @@ int alloc_workspace(tebd_ctx* c) {
 // The mixed path's digit planes, for workspaces allocated while the handle was FP64.
 int ensure_oz(tebd_ctx* c) {
   for (Slot& S : c->slots)
-    if (!S.oz && !(S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(c->capmax, c->d, c->chi_max))))
+    if (!S.oz && !(S.oz = dalloc<uint8_t>(c, (size_t)oz_slot_bytes(c->capmax, c->d, c->chi_max, c->ss))))
       return TEBD_ERR_OOM;
   return TEBD_OK;
 }
@@ -284,7 +297,7 @@ void debug_dump(tebd_ctx* c, const char* label, int t, const void* ptr, size_t n
 }
 
 const double2* gate_ptr(const tebd_ctx* c, int i, int tidx) {
-  return c->G + ((size_t)tidx * (c->L - 2) + i) * (size_t)c->D * c->D;
+  return c->G + ((size_t)tidx * gate_sites(c) + i) * (size_t)c->D * c->D;
 }
 
 // Eigen-decomposition of the Gram matrices held in the slots of ts (H, m, kmax
@@ -563,11 +576,13 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
   if (mixed)
     for (auto& T : ts)
       if (int r = ensure_oz(T.h)) return r;
+  const bool two = c->ss;  // super sites: theta~ = B_i B_{i+1}, one cut, B_{i+1} = V^+
   for (auto& T : ts) {
     const tebd_ctx* o = T.h;
-    T.chl = o->chi[T.i]; T.c1 = o->chi[T.i + 1]; T.c2 = o->chi[T.i + 2]; T.chr = o->chi[T.i + 3];
+    T.chl = o->chi[T.i]; T.c1 = o->chi[T.i + 1]; T.c2 = o->chi[T.i + 2];
+    T.chr = two ? T.c2 : o->chi[T.i + 3];
     T.m1 = T.chl * o->d;
-    T.n1 = o->d * o->d * T.chr;
+    T.n1 = (two ? o->d : o->d * o->d) * T.chr;
   }
   // theta~ = B_i B_{i+1} B_{i+2}; C = G theta~; Gram H1 = (lam C)(lam C)^+
   {
@@ -578,8 +593,10 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       const int d = o->d, D = o->D;
       const Slot& S = o->slots[T.slot];
       g1.add(T.chl * d, d * T.c2, T.c1, o->B[T.i], T.c1, o->B[T.i + 1], (long long)d * T.c2, S.X, (long long)d * T.c2);
-      g2.add(T.chl * d * d, d * T.chr, T.c2, S.X, T.c2, o->B[T.i + 2], (long long)d * T.chr, S.Th, (long long)d * T.chr);
-      GemmProb& p3 = g3.add(D, T.chr, D, gate_ptr(o, T.i, tidx), D, S.Th, T.chr, S.Cb, T.chr);
+      if (!two)
+        g2.add(T.chl * d * d, d * T.chr, T.c2, S.X, T.c2, o->B[T.i + 2], (long long)d * T.chr, S.Th,
+               (long long)d * T.chr);
+      GemmProb& p3 = g3.add(D, T.chr, D, gate_ptr(o, T.i, tidx), D, two ? S.X : S.Th, T.chr, S.Cb, T.chr);
       p3.batch = T.chl;
       p3.sA = 0;
       p3.sB = p3.sC = (long long)D * T.chr;
@@ -592,7 +609,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
       const double d = T.h->d, D = T.h->D;
-      wc += 8.0 * ((double)T.chl * d * d * T.c2 * T.c1 + (double)T.chl * d * d * d * T.chr * T.c2 +
+      wc += 8.0 * ((double)T.chl * d * d * T.c2 * T.c1 + (two ? 0.0 : (double)T.chl * d * d * d * T.chr * T.c2) +
                    D * D * T.chr * T.chl);
       wg += 4.0 * (double)T.m1 * T.m1 * T.n1;
     }
@@ -606,8 +623,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
           const Slot& S = o->slots[T.slot];
           o1.push_back(oz_plain(o->B[T.i], T.c1, o->B[T.i + 1], 1, (long long)d * T.c2, 0, T.chl * d, d * T.c2, T.c1,
                                 S.X, (long long)d * T.c2, 1.0, S.oz));
-          o2.push_back(oz_plain(S.X, T.c2, o->B[T.i + 2], 1, (long long)d * T.chr, 0, T.chl * d * d, d * T.chr, T.c2,
-                                S.Th, (long long)d * T.chr, 1.0, S.oz));
+          if (!two)
+            o2.push_back(oz_plain(S.X, T.c2, o->B[T.i + 2], 1, (long long)d * T.chr, 0, T.chl * d * d, d * T.chr,
+                                  T.c2, S.Th, (long long)d * T.chr, 1.0, S.oz));
         }
         c->launches += oz_gemm_launch(o1, c->d_status, s);
         c->launches += oz_gemm_launch(o2, c->d_status, s);
@@ -687,7 +705,7 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     double wc = 0.0, wg = 0.0;
     for (auto& T : ts) {
       wc += 8.0 * (double)T.m1 * T.chi1 * T.n1;
-      wg += 4.0 * (double)T.m2 * T.m2 * T.n2;
+      if (!two) wg += 4.0 * (double)T.m2 * T.m2 * T.n2;
     }
     {
       ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
@@ -703,11 +721,25 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
         c->launches += g6.launch(s, tf32, c->d_status);
       }
     }
-    if (!c->randomized) {
+    if (!c->randomized && !two) {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
       c->launches += mixed ? oz_gemm_launch(oz7, c->d_status, s) : g7.launch(s);
     }
     if (int r = check_launch(c)) return r;
+  }
+  if (two) {  // B_{i+1} = V^+ (chi' x d chr, rows orthonormal)
+    for (auto& T : ts) {
+      const Slot& S = T.h->slots[T.slot];
+      if (cudaMemcpyAsync(T.h->B[T.i + 1], S.V1h, sizeof(double2) * (size_t)T.chi1 * T.n1, cudaMemcpyDeviceToDevice,
+                          s) != cudaSuccess)
+        return fail_cuda(c);
+    }
+    for (auto& T : ts) {
+      T.h->chi[T.i + 1] = T.chi1;
+      T.h->w_total += T.w1;
+      T.h->gate_updates += 1;
+    }
+    return check_launch(c);
   }
   if (c->randomized) {
     if (int r = rand_cut(c, ts, true)) return r;
@@ -784,8 +816,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
 int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, int tidx) {
   struct Pending { tebd_ctx* h; int i; };
   std::vector<Pending> rest;
+  const int stride = c->ss ? 2 : 3, span = c->ss ? 1 : 2;
   for (tebd_ctx* h : hs)
-    for (int i = residue; i + 2 < h->L; i += 3) rest.push_back({h, i});
+    for (int i = residue; i + span < h->L; i += stride) rest.push_back({h, i});
   for (tebd_ctx* h : hs)  // a randomized simulation needs the workspace arenas (switched on late)
     if (h->randomized)
       if (int r = u1_alloc_slots(h, (int)h->slots.size())) return r;
@@ -810,7 +843,7 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
       T.h = p.h;
       T.i = p.i;
       T.slot = taken;
-      T.call = p.h->rcall + 2 * ((p.i - residue) / 3);
+      T.call = p.h->rcall + 2 * ((p.i - residue) / stride);
       ts.push_back(T);
       if (k) ++*k; else used.push_back({p.h, 1});
     }
@@ -818,16 +851,16 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
     rest.swap(later);
   }
   for (tebd_ctx* h : hs)
-    for (int i = residue; i + 2 < h->L; i += 3) h->rcall += 2;
+    for (int i = residue; i + span < h->L; i += stride) h->rcall += 2;
   return TEBD_OK;
 }
 
 int run_layer(tebd_ctx* c, int residue, int tidx) { return run_layer_multi(c, {c}, residue, tidx); }
 
 int ensure_measure_ws(tebd_ctx* c) {
-  if (!c->mN) {
-    c->mC = dalloc<double2>(c, c->L);
-    c->mN = dalloc<double>(c, c->L);
+  if (!c->mN) {  // super sites: two physical densities per site, 2L - 1 physical bonds
+    c->mC = dalloc<double2>(c, c->ss ? 2 * c->L : c->L);
+    c->mN = dalloc<double>(c, c->ss ? 2 * c->L : c->L);
     if (!c->mC || !c->mN) return TEBD_ERR_OOM;
   }
   if (c->u1 && c->have_charges) return TEBD_OK;  // the blocked correlators use their own arena
@@ -924,6 +957,22 @@ int tebd_gate_host(int L, int n_max, double U, double J, double J_NNN, double K,
   return TEBD_OK;
 }
 
+int tebd_gate_host_supersite(int L, int n_max, double U, double J, double J_NNN, double K, double j_c, int k,
+                             double tau, double* out) {
+  const int L_e = (L + L % 2) / 2;
+  if (L < 3 || n_max < 1 || n_max > 4 || k < 1 || k > L_e - 1 || !out) return TEBD_ERR_ARG;
+  if (!is_fin(U) || !is_fin(J) || !is_fin(J_NNN) || !is_fin(K) || !is_fin(j_c) || !is_fin(tau)) return TEBD_ERR_ARG;
+  try {
+    std::vector<std::complex<double>> G;
+    const bool ok = build_gate_supersite(L, n_max, U, J, J_NNN, K, j_c, k, tau, G, 60);
+    std::memcpy(out, G.data(), G.size() * sizeof(std::complex<double>));
+    if (!ok) return TEBD_ERR_NOT_CONVERGED;
+  } catch (...) {
+    return TEBD_ERR_OOM;
+  }
+  return TEBD_OK;
+}
+
 int tebd_gate_host_sweeps(int L, int n_max, double U, double J, double J_NNN, double K, double j_c, int j,
                           double tau, int max_sweeps, double* out) {
   if (L < 3 || n_max < 1 || n_max > 7 || j < 1 || j > L - 2 || !out || max_sweeps < 1) return TEBD_ERR_ARG;
@@ -939,11 +988,15 @@ int tebd_gate_host_sweeps(int L, int n_max, double U, double J, double J_NNN, do
   return TEBD_OK;
 }
 
-int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K, double j_c, double dt,
-                tebd_handle* out) {
+}  // extern "C"
+
+namespace {
+
+// L is the chain the MPS runs on (super sites when ss); L_phys the physical length.
+int create_impl(int L, int L_phys, bool ss, int n_max, int chi_max, double U, double J, double J_NNN, double K,
+                double j_c, double dt, tebd_handle* out) {
   if (!out) return TEBD_ERR_ARG;
   *out = nullptr;
-  if (L < 3 || n_max < 1 || n_max > 7 || chi_max < 1) return TEBD_ERR_ARG;
   if (!is_fin(U) || !is_fin(J) || !is_fin(J_NNN) || !is_fin(K) || !is_fin(j_c) || !is_fin(dt) || !(dt > 0))
     return TEBD_ERR_ARG;
   tebd_ctx* c = nullptr;
@@ -952,7 +1005,11 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
   } catch (...) {
     return TEBD_ERR_OOM;
   }
-  c->L = L; c->n_max = n_max; c->d = n_max + 1; c->D = c->d * c->d * c->d; c->chi_max = chi_max;
+  c->L = L; c->n_max = n_max; c->chi_max = chi_max;
+  c->ss = ss;
+  c->L_phys = L_phys;
+  c->d = ss ? (n_max + 1) * (n_max + 1) : n_max + 1;
+  c->D = ss ? c->d * c->d : c->d * c->d * c->d;
   c->U = U; c->J = J; c->Jnnn = J_NNN; c->K = K; c->jc = j_c; c->dt = dt;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
@@ -998,6 +1055,24 @@ int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN,
   return TEBD_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int tebd_create(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K, double j_c, double dt,
+                tebd_handle* out) {
+  if (out) *out = nullptr;
+  if (L < 3 || n_max < 1 || n_max > 7 || chi_max < 1) return TEBD_ERR_ARG;
+  return create_impl(L, L, false, n_max, chi_max, U, J, J_NNN, K, j_c, dt, out);
+}
+
+int tebd_create_supersite(int L, int n_max, int chi_max, double U, double J, double J_NNN, double K, double j_c,
+                          double dt, tebd_handle* out) {
+  if (out) *out = nullptr;
+  if (L < 3 || n_max < 1 || n_max > 4 || chi_max < 1) return TEBD_ERR_ARG;
+  return create_impl((L + L % 2) / 2, L, true, n_max, chi_max, U, J, J_NNN, K, j_c, dt, out);
+}
+
 int tebd_set_option(tebd_handle h, const char* key, double value) {
   CHECK_HANDLE(h);
   if (!key || !is_fin(value)) return TEBD_ERR_ARG;
@@ -1013,6 +1088,7 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
     h->precision = (int)value;
   } else if (k == "trotter_order") {
     if (value != 2.0 && value != 4.0) return TEBD_ERR_ARG;
+    if (h->ss && value != 2.0) return TEBD_ERR_ARG;  // the super-site split is second order
     if ((int)value != h->order) {
       if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess) return fail_cuda(h);
       h->order = (int)value;
@@ -1033,7 +1109,7 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
     }
   } else if (k == "randomized") {
     if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
-    if (value == 1.0 && h->u1) return TEBD_ERR_ARG;
+    if (value == 1.0 && (h->u1 || h->ss)) return TEBD_ERR_ARG;
     h->randomized = (value == 1.0);
   } else if (k == "oversample") {
     if (value < 0 || value > 4096 || value != std::floor(value)) return TEBD_ERR_ARG;
@@ -1043,7 +1119,7 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
     h->power_iters = (int)value;
   } else if (k == "u1") {
     if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
-    if (value == 1.0 && h->randomized) return TEBD_ERR_ARG;
+    if (value == 1.0 && (h->randomized || h->ss)) return TEBD_ERR_ARG;
     if ((value == 1.0) != h->u1) {
       if (!h->slots.empty()) return TEBD_ERR_STATE;  // the workspace is laid out for one form
       h->u1 = (value == 1.0);
@@ -1080,9 +1156,16 @@ int tebd_set_stream(tebd_handle h, void* cuda_stream) {
 int tebd_init_product(tebd_handle h, const int* occ) {
   CHECK_HANDLE(h);
   if (!occ) return TEBD_ERR_ARG;
-  for (int k = 0; k < h->L; ++k)
+  const int n_occ = h->ss ? h->L_phys : h->L;
+  for (int k = 0; k < n_occ; ++k)
     if (occ[k] < 0 || occ[k] > h->n_max) return TEBD_ERR_ARG;
-  if (cudaMemcpyAsync(h->d_occ, occ, h->L * sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+  std::vector<int> sig(occ, occ + h->L);
+  if (h->ss) {  // super site k holds physical sites (2k, 2k+1), sigma = s_a (n_max + 1) + s_b; a padded site is empty
+    const int dp = h->n_max + 1;
+    for (int k = 0; k < h->L; ++k)
+      sig[k] = occ[2 * k] * dp + (2 * k + 1 < h->L_phys ? occ[2 * k + 1] : 0);
+  }
+  if (cudaMemcpyAsync(h->d_occ, sig.data(), h->L * sizeof(int), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return fail_cuda(h);
   h->launches += launch_init_product(h->dB, h->dlam, h->d_occ, h->L, h->d, h->stream);
   if (int r = check_launch(h)) return r;
@@ -1090,8 +1173,9 @@ int tebd_init_product(tebd_handle h, const int* occ) {
   std::fill(h->chi.begin(), h->chi.end(), 1);
   // bond charges of a product state: the boson count left of each bond
   h->q.assign(h->L + 1, std::vector<int>(1, 0));
-  for (int k = 1; k <= h->L; ++k) h->q[k][0] = h->q[k - 1][0] + occ[k - 1];
-  h->have_charges = true;
+  if (!h->ss)
+    for (int k = 1; k <= h->L; ++k) h->q[k][0] = h->q[k - 1][0] + occ[k - 1];
+  h->have_charges = !h->ss;
   h->steps = 0;
   h->w_total = 0.0;
   h->gate_updates = 0;
@@ -1228,7 +1312,7 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
     if (hs[i]->sticky != TEBD_OK) return hs[i]->sticky;
     if (!hs[i]->have_state) return TEBD_ERR_STATE;
     if (hs[i]->device != hs[0]->device || hs[i]->precision != hs[0]->precision || hs[i]->order != hs[0]->order ||
-        hs[i]->u1 != hs[0]->u1)
+        hs[i]->u1 != hs[0]->u1 || hs[i]->ss != hs[0]->ss || hs[i]->randomized != hs[0]->randomized)
       return TEBD_ERR_ARG;
     if (hs[i]->u1 && !hs[i]->have_charges) return TEBD_ERR_STATE;
     for (int j = 0; j < i; ++j)
@@ -1258,7 +1342,7 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
 
 int tebd_layer(tebd_handle h, int residue, int full) {
   CHECK_HANDLE(h);
-  if (residue < 0 || residue > 2 || (full != 0 && full != 1)) return TEBD_ERR_ARG;
+  if (residue < 0 || residue > (h->ss ? 1 : 2) || (full != 0 && full != 1)) return TEBD_ERR_ARG;
   if (h->order != 2) return TEBD_ERR_ARG;  // the gate table holds dt/2 and dt only at order 2
   if (!h->have_state || (h->u1 && !h->have_charges)) return TEBD_ERR_STATE;
   try {
@@ -1269,11 +1353,71 @@ int tebd_layer(tebd_handle h, int residue, int full) {
   }
 }
 
+}  // extern "C"
+
+namespace {
+
+// Observables of the super-site chain on its 2L physical sites: n of positions a and b of
+// every super site; <b+ b> inside a super site (one-site term) and across a super bond
+// (b+ on position b of k, b on position a of k + 1), the latter as the transfer
+// products of the plain chain with the shifts of one position of the pair.
+int measure_supersite(tebd_ctx* h, double* n_out, double* cur_out) {
+  const int L = h->L, d = h->d, dp = h->n_max + 1, Lp = 2 * L;
+  double mbytes = 0.0;
+  for (int k = 0; k < L; ++k) mbytes += 16.0 * h->chi[k] * d * h->chi[k + 1];
+  ProfScope ps(h, TEBD_PROF_MEASURE, 3.0 * mbytes);
+  std::vector<DensityArgs> da(Lp);
+  for (int k = 0; k < L; ++k)
+    for (int pos = 0; pos < 2; ++pos)
+      da[2 * k + pos] = DensityArgs{h->B[k], h->lam[k], h->mN + 2 * k + pos, h->chi[k], d, h->chi[k + 1], 1 + pos, dp};
+  h->launches += launch_densities(da.data(), Lp, h->stream);
+  for (int k = 0; k < L; ++k)
+    h->launches += launch_pair_hop(h->B[k], h->lam[k], h->chi[k], d, h->chi[k + 1], dp, h->mC + 2 * k, h->stream);
+  const long long capmax = std::max<long long>(1, *std::max_element(h->cap.begin(), h->cap.end()));
+  const long long big = capmax * d * capmax;
+  for (int k0 = 0; k0 < L - 1; k0 += MEAS_CHUNK) {
+    const int k1 = std::min(L - 1, k0 + MEAS_CHUNK);
+    Gemm gx(true, OP_C, OP_N), gy(true, OP_N, OP_C);
+    for (int k = k0; k < k1; ++k) {
+      const int q = k - k0;
+      const int cl = h->chi[k], cm = h->chi[k + 1], cr = h->chi[k + 2];
+      double2* P = h->mP + q * big;
+      double2* Q = h->mQ + q * big;
+      // b+ on position b of super site k (sigma -> sigma + 1), b on position a of k + 1 (sigma -> sigma - dp)
+      h->launches += launch_shift_pair(h->B[k], h->lam[k], P, cl, d, cm, 1, 1, dp, h->stream);
+      h->launches += launch_shift_pair(h->B[k + 1], nullptr, Q, cm, d, cr, dp, 2, dp, h->stream);
+      gx.add(cm, cm, cl * d, P, cm, h->B[k], cm, h->mX + q * capmax * capmax, cm);
+      gy.add(cm, cm, d * cr, Q, (long long)d * cr, h->B[k + 1], (long long)d * cr, h->mY + q * capmax * capmax, cm);
+    }
+    h->launches += gx.launch(h->stream);
+    h->launches += gy.launch(h->stream);
+    for (int k = k0; k < k1; ++k) {
+      const int q = k - k0;
+      h->launches += launch_trace_product(h->mX + q * capmax * capmax, h->mY + q * capmax * capmax, h->chi[k + 1],
+                                          h->mC + 2 * k + 1, h->stream);
+    }
+  }
+  if (int r = check_launch(h)) return r;
+  if (int r = ensure_pinned(h, 3 * (size_t)Lp + 8)) return r;
+  cudaMemcpyAsync(h->h_pinned, h->mN, Lp * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaMemcpyAsync(h->h_pinned + Lp, h->mC, (Lp - 1) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
+  if (int r = sync(h)) return r;
+  if (n_out) std::memcpy(n_out, h->h_pinned, Lp * sizeof(double));
+  if (cur_out)
+    for (int j = 0; j < Lp - 1; ++j) cur_out[j] = 2.0 * h->J * h->h_pinned[Lp + 2 * j + 1];
+  return TEBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int tebd_measure(tebd_handle h, double* n_out, double* cur_out) {
   CHECK_HANDLE(h);
   if (!h->have_state) return TEBD_ERR_STATE;
   try {
     if (int r = ensure_measure_ws(h)) return r;
+    if (h->ss) return measure_supersite(h, n_out, cur_out);
     const int L = h->L, d = h->d;
     double mbytes = 0.0;
     for (int k = 0; k < L; ++k) mbytes += 16.0 * h->chi[k] * d * h->chi[k + 1];

@@ -10,6 +10,7 @@
 #include "ptebd_internal.h"
 
 #include <cmath>
+#include <algorithm>
 #include <complex>
 #include <vector>
 
@@ -135,6 +136,88 @@ bool build_gate(int L, int n_max, double U, double J, double Jnnn, double K, dou
       G[(size_t)r * D + c] = acc;
     }
   return ok;
+}
+
+// ---- super sites (pairs of physical sites, the paper's scheme of Sec. II B) ----------------
+// Super site k (1-based) holds physical sites 2k-1 and 2k of the chain padded to even
+// length L' = L + (L mod 2); its basis index is sigma = s_a d + s_b.  The term of super
+// bond (k, k+1) acts on physical sites 2k-1 .. 2k+2 (positions 0..3, position 3 fastest):
+// the couplings between the two super sites (NN hop of positions 1, 2; NNN hops 0-2 and
+// 1-3) in full, and the terms inside each super site (its NN hop and on-site terms)
+// divided by the number of super bonds that contain it, so that the bond terms sum to
+// eq. (1) on the padded chain.
+std::vector<cd> supersite_bond_term(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int k) {
+  const int d = n_max + 1, D = d * d * d * d;
+  const int Lp = L + (L % 2), Le = Lp / 2;
+  std::vector<cd> h((size_t)D * D, cd(0, 0));
+  auto mult = [&](int kk) { return (kk >= 2 ? 1 : 0) + (kk <= Le - 1 ? 1 : 0); };
+  for (int a = 0; a < D; ++a) {
+    int n[4] = {a / (d * d * d), (a / (d * d)) % d, (a / d) % d, a % d};
+    double diag = 0;
+    for (int pos = 0; pos < 4; ++pos) {
+      const int kk = (pos < 2) ? k : k + 1;
+      const int site = 2 * kk - 1 + (pos % 2);
+      const double x = site - jc;
+      diag += (0.5 * U * n[pos] * (n[pos] - 1) + 0.5 * K * x * x * n[pos]) / mult(kk);
+    }
+    h[(size_t)a * D + a] += diag;
+    // hops b+_p b_q + h.c.: (position pair, amplitude)
+    const int pairs[5][2] = {{1, 2}, {0, 2}, {1, 3}, {0, 1}, {2, 3}};
+    const double amps[5] = {-J, -Jnnn, -Jnnn, -J / mult(k), -J / mult(k + 1)};
+    for (int e = 0; e < 5; ++e) {
+      for (int dir = 0; dir < 2; ++dir) {
+        const int p = dir ? pairs[e][1] : pairs[e][0], q = dir ? pairs[e][0] : pairs[e][1];  // b+_p b_q
+        if (n[q] == 0 || n[p] == n_max) continue;
+        int m[4] = {n[0], n[1], n[2], n[3]};
+        const double amp = std::sqrt((double)(m[p] + 1) * m[q]);
+        m[p] += 1;
+        m[q] -= 1;
+        const int b = ((m[0] * d + m[1]) * d + m[2]) * d + m[3];
+        h[(size_t)b * D + a] += amps[e] * amp;
+      }
+    }
+  }
+  return h;
+}
+
+// G = exp(-i h tau) for a Hermitian h that conserves the total occupation (occ[x] of basis
+// state x): each occupation block diagonalised on its own by the cyclic Jacobi solver.
+bool exp_by_occupation(const std::vector<cd>& h, const std::vector<int>& occ, double tau, std::vector<cd>& G,
+                       int max_sweeps) {
+  const int D = (int)occ.size();
+  G.assign((size_t)D * D, cd(0, 0));
+  const int nmax = *std::max_element(occ.begin(), occ.end());
+  bool ok = true;
+  for (int t = 0; t <= nmax; ++t) {
+    std::vector<int> mem;
+    for (int x = 0; x < D; ++x)
+      if (occ[x] == t) mem.push_back(x);
+    const int n = (int)mem.size();
+    if (n == 0) continue;
+    std::vector<cd> A((size_t)n * n), V;
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) A[(size_t)r * n + c] = h[(size_t)mem[r] * D + mem[c]];
+    std::vector<double> E;
+    ok = hermitian_jacobi(n, A, E, V, max_sweeps) && ok;
+    std::vector<cd> ph(n);
+    for (int q = 0; q < n; ++q) ph[q] = std::exp(cd(0, -E[q] * tau));
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        cd acc(0, 0);
+        for (int q = 0; q < n; ++q) acc += V[(size_t)r * n + q] * ph[q] * std::conj(V[(size_t)c * n + q]);
+        G[(size_t)mem[r] * D + mem[c]] = acc;
+      }
+  }
+  return ok;
+}
+
+bool build_gate_supersite(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int k, double tau,
+                          std::vector<cd>& G, int max_sweeps) {
+  const int d = n_max + 1, D = d * d * d * d;
+  std::vector<cd> h = supersite_bond_term(L, n_max, U, J, Jnnn, K, jc, k);
+  std::vector<int> occ(D);
+  for (int x = 0; x < D; ++x) occ[x] = x / (d * d * d) + (x / (d * d)) % d + (x / d) % d + x % d;
+  return exp_by_occupation(h, occ, tau, G, max_sweeps);
 }
 
 }  // namespace ptebd

@@ -161,7 +161,8 @@ __global__ void k_densities(const __grid_constant__ DensityBatch db) {
     const int s = (int)((e / A.chr) % A.d);
     const double2 v = A.B[e];
     const double l = A.lam[a];
-    acc += l * l * (double)s * (v.x * v.x + v.y * v.y);
+    const int w = (A.wmode == 1) ? s / A.wd : (A.wmode == 2 ? s % A.wd : s);
+    acc += l * l * (double)w * (v.x * v.x + v.y * v.y);
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) *A.out = acc;
@@ -304,6 +305,62 @@ int launch_densities(const DensityArgs* a, int n, cudaStream_t s) {
     ++launches;
   }
   return launches;
+}
+
+__global__ void k_shift_pair(const double2* B, const double* lam, double2* out, int chl, int d, int chr, int shift,
+                             int mode, int wd) {
+  const long long total = (long long)chl * d * chr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / ((long long)d * chr));
+    const int s = (int)((e / chr) % d);
+    const int c = (int)(e % chr);
+    const int w = (mode == 1) ? s % wd : s / wd;
+    double2 v = make_double2(0.0, 0.0);
+    if (w < wd - 1 && s + shift < d) {
+      const double f = (lam ? lam[a] * lam[a] : 1.0) * sqrt((double)(w + 1));
+      const double2 x = B[((long long)a * d + s + shift) * chr + c];
+      v = make_double2(f * x.x, f * x.y);
+    }
+    out[e] = v;
+  }
+}
+
+__global__ void k_pair_hop(const double2* B, const double* lam, int chl, int d, int chr, int wd, double2* out) {
+  __shared__ double sr[32], si[32];
+  double re = 0.0, im = 0.0;
+  const long long total = (long long)chl * d * chr;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int a = (int)(e / ((long long)d * chr));
+    const int s = (int)((e / chr) % d);  // sigma' = s'_a wd + s'_b
+    const int c = (int)(e % chr);
+    const int sa = s / wd, sb = s % wd;
+    if (sa >= wd - 1 || sb < 1) continue;
+    const double f = lam[a] * lam[a] * sqrt((double)(sa + 1) * sb);
+    const double2 x = B[e];                                          // B[a, sigma', b]
+    const double2 y = B[((long long)a * d + s + wd - 1) * chr + c];  // B[a, (s'_a + 1, s'_b - 1), b]
+    re = fma(f, y.x * x.x + y.y * x.y, re);                         // conj(y) x
+    im = fma(f, y.x * x.y - y.y * x.x, im);
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) { sr[threadIdx.x >> 5] = re; si[threadIdx.x >> 5] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0, m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { r += sr[w]; m += si[w]; }
+    *out = make_double2(r, m);
+  }
+}
+
+int launch_shift_pair(const double2* B, const double* lam, double2* out, int chl, int d, int chr, int shift, int mode,
+                      int wd, cudaStream_t s) {
+  k_shift_pair<<<grid_for((long long)chl * d * chr), 256, 0, s>>>(B, lam, out, chl, d, chr, shift, mode, wd);
+  return 1;
+}
+
+int launch_pair_hop(const double2* B, const double* lam, int chl, int d, int chr, int wd, double2* out, cudaStream_t s) {
+  k_pair_hop<<<1, 256, 0, s>>>(B, lam, chl, d, chr, wd, out);
+  return 1;
 }
 
 int launch_shift_left(const double2* B, const double* lam, double2* out, int chl, int d, int chr, cudaStream_t s) {

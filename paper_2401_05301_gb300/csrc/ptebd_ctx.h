@@ -42,6 +42,10 @@ struct U1Work;  // workspace of the blocked form (u1.cu)
 
 struct tebd_ctx {
   int L = 0, n_max = 0, d = 0, D = 0, chi_max = 0;
+  // super sites (tebd_create_supersite): the MPS runs on L = L_eff super sites of local
+  // dimension d = (n_max + 1)^2 with two-site gates of dimension D = d^2; L_phys physical sites
+  bool ss = false;
+  int L_phys = 0;
   double U = 0, J = 0, Jnnn = 0, K = 0, jc = 0, dt = 0;
   double w_cut = 0.0, eps_rel = 1e-12;
   int precision = 0, max_slots = 0;

@@ -16,6 +16,12 @@ std::vector<std::complex<double>> three_site_term(int L, int n_max, double U, do
 // max_sweeps: limit of the cyclic Jacobi eigen-solver (false if it did not converge).
 bool build_gate(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int j,
                 double tau, std::vector<std::complex<double>>& G, int max_sweeps = 60);
+// Super sites (pairs of physical sites): the term of super bond k (1-based) on the chain
+// padded to even length, d^4 x d^4 over positions (2k-1, 2k, 2k+1, 2k+2), and its gate.
+std::vector<std::complex<double>> supersite_bond_term(int L, int n_max, double U, double J, double Jnnn, double K,
+                                                      double jc, int k);
+bool build_gate_supersite(int L, int n_max, double U, double J, double Jnnn, double K, double jc, int k,
+                          double tau, std::vector<std::complex<double>>& G, int max_sweeps = 60);
 
 // ---- grouped GEMM (kernels_gemm.cu) ------------------------------------------
 // C = alpha * op(A) * op(B) [+ C], op in {N, C = conjugate transpose, CJ = conjugate}; complex
@@ -38,6 +44,7 @@ struct GemmProb {
   int M, N, K, batch;
   int red_div, row_div, col_div, accumulate;
   int herm;  // result is Hermitian (M == N, B = A^+): only lower tiles are computed, then mirrored
+  const double* s_red_b;  // optional factor of B along the reduction index (red_div as s_red)
 };
 
 struct GemmBatch {
@@ -259,6 +266,7 @@ struct DensityArgs {
   const double* lam;
   double* out;
   int chl, d, chr;
+  int wmode, wd;  // occupation of local state s: s (0), s / wd (1, first site of a pair), s % wd (2)
 };
 int launch_densities(const DensityArgs* a, int n, cudaStream_t s);
 
@@ -267,6 +275,14 @@ int launch_shift_left(const double2* B, const double* lam, double2* out, int chl
                       cudaStream_t s);
 // Q'[c,(t,b)] = sqrt(t+1) B[c,t+1,b] (t < d-1), 0 for t = d-1
 int launch_shift_right(const double2* B, double2* out, int chl, int d, int chr, cudaStream_t s);
+// out[(a,s),c] = f lam_a^2 sqrt(w(s)+1) B[a, s+shift, c] where w(s) < wd - 1, else 0, with
+// w(s) = s % wd (mode 1) or s / wd (mode 2); f = 1 and lam optional (NULL: no lam^2).  The
+// raising operator of one site of a super site (pairs of sites, sigma = s_a wd + s_b).
+int launch_shift_pair(const double2* B, const double* lam, double2* out, int chl, int d, int chr, int shift, int mode,
+                      int wd, cudaStream_t s);
+// out = sum_{a,b} lam_a^2 sum_sigma' sqrt(s'_a + 1) sqrt(s'_b) conj(B[a, sigma' + wd - 1, b]) B[a, sigma', b]
+// over s'_a < wd - 1, s'_b >= 1: <b+_(2k-1) b_(2k)> inside super site k.
+int launch_pair_hop(const double2* B, const double* lam, int chl, int d, int chr, int wd, double2* out, cudaStream_t s);
 // out = sum_{c,c'} X[c,c'] Yt[c',c]
 int launch_trace_product(const double2* X, const double2* Yt, int chi, double2* out, cudaStream_t s);
 

@@ -84,3 +84,40 @@ def test_host_jacobi_sweep_limit_reports_not_converged(lib):
     out = np.empty(2 * 64 ** 2)
     assert lib.tebd_gate_host_sweeps(L, n_max, U, J, Jnnn, K, jc, j, tau, 0,
                                      out.ctypes.data_as(binding._P_double)) == -1
+
+
+@pytest.mark.parametrize("L,n_max", [(7, 1), (8, 2), (5, 3), (6, 4)])
+def test_host_supersite_gate_matches_oracle(lib, L, n_max):
+    """tebd_gate_host_supersite (block-wise exponential of the super bond term)
+    against the super-site oracle's exp(-i h_k tau) of its own bond term, every bond."""
+    from oracle import supersite
+    U, J, Jnnn, K, jc, tau = 3.0, 1.0, 0.2, 0.05, (L + 1) / 2, 0.025
+    L_eff = supersite.padded_length(L) // 2
+    for k in range(1, L_eff):
+        G = binding.gate_host_supersite(L, n_max, U, J, Jnnn, K, jc, k, tau)
+        ref = model.gate(supersite.bond_term(k, L, n_max, U, J, Jnnn, K, jc), tau)
+        assert np.max(np.abs(G - ref)) < 1e-13, k
+        assert np.max(np.abs(G.conj().T @ G - np.eye(len(G)))) < 1e-13
+
+
+def test_host_supersite_gate_paper_setup(lib):
+    """L = 121 padded to 122 (61 super sites), d = 5, Table Ib set a: the end bonds carry
+    the largest trap terms (|h| ~ 260, so |E tau| ~ 20 rad at tau = dt, and each side's
+    phases carry rounding of order eps |E tau| over blocks of up to 85 states: bound 5e-13)."""
+    import workloads
+    from oracle import supersite
+    wl = workloads.paper_run("a", 27, 40)
+    for k in (1, 30, 60):
+        G = binding.gate_host_supersite(wl.L, wl.n_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, k, wl.dt)
+        ref = model.gate(supersite.bond_term(k, wl.L, wl.n_max, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc), wl.dt)
+        assert np.max(np.abs(G - ref)) < 5e-13
+        assert np.max(np.abs(G.conj().T @ G - np.eye(len(G)))) < 1e-13
+
+
+def test_host_supersite_gate_rejects_bad_args(lib):
+    out = np.empty(2 * 5 ** 8)
+    ptr = out.ctypes.data_as(binding._P_double)
+    assert lib.tebd_gate_host_supersite(2, 1, 1, 1, 0, 0, 1, 1, 0.1, ptr) == -1   # L < 3
+    assert lib.tebd_gate_host_supersite(8, 1, 1, 1, 0, 0, 1, 4, 0.1, ptr) == -1   # k > L_eff - 1
+    assert lib.tebd_gate_host_supersite(8, 5, 1, 1, 0, 0, 1, 1, 0.1, ptr) == -1   # n_max > 4
+    assert lib.tebd_gate_host_supersite(8, 2, 1, float("inf"), 0, 0, 1, 1, 0.1, ptr) == -1
