@@ -1457,7 +1457,13 @@ int tebd_measure(tebd_handle h, double* n_out, double* cur_out) {
     if (int r = ensure_pinned(h, 3 * (size_t)L + 8)) return r;
     cudaMemcpyAsync(h->h_pinned, h->mN, L * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     cudaMemcpyAsync(h->h_pinned + L, h->mC, (L - 1) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream);
+    int* h_status = reinterpret_cast<int*>(h->h_pinned + 3 * (size_t)L);  // the tensor-core waits' status
+    cudaMemcpyAsync(h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (int r = sync(h)) return r;
+    if (*h_status != 0) {
+      h->sticky = *h_status;
+      return *h_status;
+    }
     if (n_out) std::memcpy(n_out, h->h_pinned, L * sizeof(double));
     if (cur_out)
       for (int k = 0; k < L - 1; ++k) cur_out[k] = 2.0 * h->J * h->h_pinned[L + 2 * k + 1];

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const __grid_constant__ GemmBa
         if (OPB == OP_N) v = B[(long long)gk * P.ldb + gj];
         else if (OPB == OP_C) v = A_::cj(B[(long long)gj * P.ldb + gk]);
         else v = A_::cj(B[(long long)gk * P.ldb + gj]);
+        if (P.s_red_b) v = A_::scale(v, P.s_red_b[gk / P.red_div]);
       }
       Bs[kk][j] = v;
     }
@@ -190,7 +191,8 @@ int Gemm::launch(cudaStream_t s, bool mixed, int* status) {
     std::vector<TcGemmProb> tp;
     bool eligible = true;
     for (const GemmProb& p : probs_) {
-      if (p.s_red || p.s_row || p.s_col || p.accumulate || p.herm || p.alpha_im != 0.0) eligible = false;
+      if (p.s_red || p.s_red_b || p.s_row || p.s_col || p.accumulate || p.herm || p.alpha_im != 0.0)
+        eligible = false;
       TcGemmProb q{};
       q.A = static_cast<const double2*>(p.A);
       q.B = static_cast<const double2*>(p.B);

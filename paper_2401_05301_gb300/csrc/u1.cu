@@ -283,10 +283,107 @@ __global__ void k_kept_gather(const KeptGather* __restrict__ kg) {
   }
 }
 
+// Blocks decomposed from the right Gram matrix: U holds the right singular vectors z_k
+// (K rows of length n).  The rows the truncation expects are Y_k = s_k z_k^+, with
+// s_k = ||lam P z_k|| (second-order accurate in the eigenvector error, like the row norms
+// of the left projection) from T = (lam P) [z_0 .. z_{K-1}] (b x K).
+struct RightRows {
+  const double2* U;
+  double2* Y;
+  const double2* T;
+  int K, n, b;
+};
+
+// Y = conj(U): the rows z_k^+ (also the second operand of T = (lam P) Y^+)
+__global__ void k_right_conj(const RightRows* __restrict__ rr) {
+  const RightRows R = rr[blockIdx.y];
+  const int k = blockIdx.x;
+  if (k >= R.K) return;
+  for (int j = threadIdx.x; j < R.n; j += blockDim.x) {
+    const double2 u = R.U[(size_t)k * R.n + j];
+    R.Y[(size_t)k * R.n + j] = make_double2(u.x, -u.y);
+  }
+}
+
+// Y_k *= ||T[:, k]||
+__global__ void k_right_scale(const RightRows* __restrict__ rr) {
+  __shared__ double sh[32];
+  __shared__ double s_sh;
+  const RightRows R = rr[blockIdx.y];
+  const int k = blockIdx.x;
+  if (k >= R.K) return;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < R.b; r += blockDim.x) {
+    const double2 t = R.T[(size_t)r * R.K + k];
+    acc = fma(t.x, t.x, fma(t.y, t.y, acc));
+  }
+  acc = warp_sum_d(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    s_sh = sqrt(t);
+  }
+  __syncthreads();
+  const double sk = s_sh;
+  for (int j = threadIdx.x; j < R.n; j += blockDim.x) {
+    double2& y = R.Y[(size_t)k * R.n + j];
+    y = make_double2(sk * y.x, sk * y.y);
+  }
+}
+
 // f[i] = lam[i]^2 w[i] (the reduction factors of the correlator's left product)
 __global__ void k_lam2w(const double* __restrict__ lam, const double* __restrict__ w, double* __restrict__ f, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) f[i] = lam[i] * lam[i] * w[i];
+}
+
+// The gate on the compact theta~: C_Delta = G_Delta theta~_Delta for every conserved
+// total Delta, G_Delta an nd x nd block (nd <= 48 for d <= 8) and theta~_Delta nd x N
+// (row stride N).  A thread takes one column: the nd entries in registers, G in shared
+// memory (read by all lanes at once), the nd outputs accumulated in sigma order.  The
+// reduction is too short for the tensor cores' accumulation (a single k-step), so the
+// product stays on the FP64 pipe, with no padding of the small dimension.
+struct GateBlk {
+  const double2* G;
+  const double2* X;
+  double2* C;
+  long long N;
+  int nd;
+  int blk0;  // first block of this problem in the launch
+};
+
+template <int NDM>
+__global__ void __launch_bounds__(128) k_gate_blocks(const GateBlk* __restrict__ gb, int nprob) {
+  __shared__ double2 Gs[NDM * NDM];
+  int lo = 0, hi = nprob - 1;  // the problem whose blocks hold blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (gb[mid].blk0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const GateBlk P = gb[lo];
+  const int nd = P.nd;
+  for (int e = threadIdx.x; e < nd * nd; e += blockDim.x) Gs[e] = P.G[e];
+  __syncthreads();
+  const long long j = (long long)(blockIdx.x - P.blk0) * blockDim.x + threadIdx.x;
+  if (j >= P.N) return;
+  double2 x[NDM];
+#pragma unroll
+  for (int q = 0; q < NDM; ++q) x[q] = (q < nd) ? P.X[(long long)q * P.N + j] : make_double2(0.0, 0.0);
+  for (int r = 0; r < nd; ++r) {
+    double re = 0.0, im = 0.0;
+    const double2* g = Gs + r * nd;
+#pragma unroll
+    for (int q = 0; q < NDM; ++q) {
+      if (q < nd) {
+        const double2 a = g[q];
+        re = fma(a.x, x[q].x, fma(-a.y, x[q].y, re));
+        im = fma(a.x, x[q].y, fma(a.y, x[q].x, im));
+      }
+    }
+    P.C[(long long)r * P.N + j] = make_double2(re, im);
+  }
 }
 
 // One bond's correlator from its charge blocks: out[bond] = sum over its blocks v of
@@ -617,6 +714,43 @@ int run_prods(tebd_ctx* c, const std::vector<Prod>& ps, int engine) {
   return check_launch(c);
 }
 
+// The gate products (C = G X, G nd x nd with lda = nd, X and C nd x N with row stride N) in
+// one launch per register bucket of nd.
+int launch_gate_blocks(tebd_ctx* c, const std::vector<Prod>& ps) {
+  constexpr int NB = 4;
+  const int cap[NB] = {8, 20, 32, 48};
+  std::vector<GateBlk> bk[NB];
+  int blocks[NB] = {};
+  for (const Prod& p : ps) {
+    if (p.M != p.K || p.lda != p.K || p.ldb != p.N || p.ldc != p.N || p.opB != OP_N || p.accumulate ||
+        p.alpha != 1.0 || p.M > cap[NB - 1]) {
+      std::fprintf(stderr, "ptebd: gate block outside the gate kernel's shapes (nd = %d)\n", p.M);
+      return TEBD_ERR_STATE;
+    }
+    int b = 0;
+    while (cap[b] < p.M) ++b;
+    const long long nblk = (p.N + 127) / 128;
+    if ((long long)blocks[b] + nblk > 2000000000LL) return TEBD_ERR_STATE;
+    bk[b].push_back(GateBlk{p.A, p.B, p.C, (long long)p.N, p.M, blocks[b]});
+    blocks[b] += (int)nblk;
+  }
+  for (int b = 0; b < NB; ++b) {
+    if (bk[b].empty() || blocks[b] == 0) continue;
+    int err = TEBD_OK;
+    GateBlk* d = stage(c, bk[b], &err);
+    if (err) return err;
+    const int n = (int)bk[b].size();
+    switch (b) {
+      case 0: k_gate_blocks<8><<<blocks[b], 128, 0, c->stream>>>(d, n); break;
+      case 1: k_gate_blocks<20><<<blocks[b], 128, 0, c->stream>>>(d, n); break;
+      case 2: k_gate_blocks<32><<<blocks[b], 128, 0, c->stream>>>(d, n); break;
+      default: k_gate_blocks<48><<<blocks[b], 128, 0, c->stream>>>(d, n); break;
+    }
+    c->launches += 1;
+  }
+  return check_launch(c);
+}
+
 // ---- host: one cut (SVD) of the blocked update ---------------------------------------------
 
 struct CutBlk {
@@ -625,6 +759,11 @@ struct CutBlk {
   std::vector<int> rs;   // row start of each row group
   std::vector<int> cs;   // column start of each column group
   int kmax = 0, K = 0;   // eigenvectors possible / computed
+  // Gram side: the smaller of (lam P)(lam P)^+ (b x b, left) and (lam P)^+ (lam P) (n x n,
+  // right).  Both have the squared singular values as their non-zero eigenvalues; the
+  // right one's eigenvectors are the right singular vectors themselves.
+  bool right() const { return n < b; }
+  int g() const { return right() ? n : b; }
   int cnt = 0, kst = 0;  // kept values, their start on the new bond
   double trace = 0.0;
   size_t oP, oLam, oH, od, oe, oev, otau, op, opart, otr, oZ, oZ2, oS, owork, oU, opan, oY, oV, oW, oSn, oOut;
@@ -657,23 +796,23 @@ size_t eig_ws_bytes(int b, int kmax) {
 // arena layout of a cut's blocks (sizes known before the cut is taken)
 void layout_cut(Cut& cut, Bump& bp) {
   for (CutBlk& B : cut.blk) {
-    const size_t b = B.b, n = B.n, k = B.kmax;
+    const size_t b = B.b, n = B.n, k = B.kmax, g = B.g();  // the eigen-solver works on g x g
     B.oP = bp.take(16 * b * n);
     B.oLam = bp.take(8 * b);
-    B.oH = bp.take(16 * b * b);
-    B.od = bp.take(8 * b);
-    B.oe = bp.take(8 * b);
-    B.oev = bp.take(8 * b);
-    B.otau = bp.take(16 * b);
-    B.op = bp.take(16 * b);
+    B.oH = bp.take(16 * g * g);
+    B.od = bp.take(8 * g);
+    B.oe = bp.take(8 * g);
+    B.oev = bp.take(8 * g);
+    B.otau = bp.take(16 * g);
+    B.op = bp.take(16 * g);
     B.opart = bp.take(16 * (size_t)EIG_PARTS);
     B.otr = bp.take(8);
-    B.oZ = bp.take(8 * b * k);
-    B.oZ2 = bp.take(8 * b * k);
+    B.oZ = bp.take(8 * g * k);
+    B.oZ2 = bp.take(8 * g * k);
     B.oS = bp.take(8 * k * k);
-    B.owork = bp.take(40 * b * k);
-    B.oU = bp.take(16 * k * b);
-    B.opan = bp.take(16 * eig_panel_doubles2((int)b));
+    B.owork = bp.take(40 * g * k);
+    B.oU = bp.take(16 * k * g);
+    B.opan = bp.take(16 * eig_panel_doubles2((int)g));
     B.oY = bp.take(16 * k * n);
     B.oV = bp.take(16 * k * n);
     B.oW = bp.take(16 * k * n);
@@ -702,15 +841,33 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
   const int prec = c->precision;
   const bool mixed = prec >= 1;
   const size_t nc = cuts.size();
-  // Gram matrices H_c = (lam P_c)(lam P_c)^+
+  // Gram matrices H_c = (lam P_c)(lam P_c)^+, or (lam P_c)^+ (lam P_c) where that is smaller
   {
     double w = 0.0;
-    Gemm g(true, OP_N, OP_C);
+    Gemm g(true, OP_N, OP_C), gr(true, OP_C, OP_N);
     std::vector<OzProb> oz;
     size_t need = 0;
     for (size_t t = 0; t < nc; ++t)
       for (CutBlk& B : cuts[t]->blk) {
         char* a = bases[t];
+        if (B.right()) {  // H[i][j] = sum_r lam_r^2 conj(P[r][i]) P[r][j], n x n
+          w += 4.0 * (double)B.n * B.n * B.b;
+          if (mixed) {
+            need = std::max(need, oz_workspace_bytes(B.n, B.n, B.b, true));
+            OzProb q{};
+            q.a = OzOperand{at<double2>(a, B.oP), 1, B.n, at<double>(a, B.oLam), 1, 1};
+            q.M = q.N = B.n; q.K = B.b; q.C = at<double2>(a, B.oH); q.ldc = B.n; q.alpha = 1.0;
+            q.row_div = q.col_div = 1;
+            q.herm = q.gram = 1;
+            oz.push_back(q);
+          } else {
+            GemmProb& p = gr.add(B.n, B.n, B.b, at<double2>(a, B.oP), B.n, at<double2>(a, B.oP), B.n,
+                                 at<double2>(a, B.oH), B.n);
+            p.s_red = p.s_red_b = at<double>(a, B.oLam);
+            p.herm = 1;
+          }
+          continue;
+        }
         w += 4.0 * (double)B.b * B.b * B.n;
         if (mixed) {
           need = std::max(need, oz_workspace_bytes(B.b, B.b, B.n, true));
@@ -735,6 +892,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
       c->launches += oz_gemm_launch(oz, c->d_status, c->stream);
     } else {
       c->launches += g.launch(c->stream);
+      c->launches += gr.launch(c->stream);
     }
     if (int r = check_launch(c)) return r;
   }
@@ -745,9 +903,9 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
   for (size_t t = 0; t < nc; ++t)
     for (CutBlk& B : cuts[t]->blk) {
       jobs.push_back({t, &B});
-      if (mixed) ews = std::max(ews, eig_ws_bytes(B.b, B.kmax));
+      if (mixed) ews = std::max(ews, eig_ws_bytes(B.g(), B.kmax));
     }
-  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& x, const Job& y) { return x.B->b > y.B->b; });
+  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& x, const Job& y) { return x.B->g() > y.B->g(); });
   if (mixed)
     if (int r = ensure_ering(c, ews)) return r;
   auto mat = [&](const Job& j) {
@@ -759,7 +917,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
     M.evals = at<double>(a, B.oev); M.trace = at<double>(a, B.otr); M.Z = at<double>(a, B.oZ);
     M.Z2 = at<double>(a, B.oZ2); M.S = at<double>(a, B.oS); M.work = at<double>(a, B.owork);
     M.U = at<double2>(a, B.oU); M.pan = at<double2>(a, B.opan);
-    M.m = B.b; M.kmax = B.kmax; M.K = B.K;
+    M.m = B.g(); M.kmax = B.kmax; M.K = B.K;
     return M;
   };
   void* ozw[EIG_MAXP] = {};
@@ -767,7 +925,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
     for (int i = 0; i < EIG_MAXP; ++i) ozw[i] = c->u1w->ering[i];
   {
     double w = 0.0;
-    for (const Job& j : jobs) w += 16.0 / 3.0 * std::pow((double)j.B->b, 3);
+    for (const Job& j : jobs) w += 16.0 / 3.0 * std::pow((double)j.B->g(), 3);
     ProfScope ps(c, TEBD_PROF_TRIDIAG, w);
     for (size_t g0 = 0; g0 < jobs.size(); g0 += EIG_MAXP) {
       EigBatch eb{};
@@ -942,7 +1100,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
     for (const Job& j : jobs)
       if (j.B->K > 0) {
         vj.push_back(j);
-        w += 8.0 * (double)j.B->b * j.B->b * j.B->K + 12.0 * (double)j.B->b * j.B->K * j.B->K;
+        w += 8.0 * (double)j.B->g() * j.B->g() * j.B->K + 12.0 * (double)j.B->g() * j.B->K * j.B->K;
       }
     ProfScope ps(c, TEBD_PROF_EIGVEC, w);
     for (size_t g0 = 0; g0 < vj.size(); g0 += EIG_MAXP) {
@@ -954,17 +1112,38 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
     }
     if (int r = check_launch(c)) return r;
   }
-  // projection Y_c = U_c^+ (lam P_c)
+  // projection Y_c = U_c^+ (lam P_c); for a right Gram Y_c = diag(s) Z_c^+ (k_right_*)
   {
     double w = 0.0;
-    Gemm g(true, OP_CJ, OP_N);
+    Gemm g(true, OP_CJ, OP_N), gt(true, OP_N, OP_C);
     std::vector<OzProb> oz;
+    std::vector<RightRows> rr;
+    int rmaxK = 0;
     size_t need = 0;
     for (size_t t = 0; t < nc; ++t)
       for (CutBlk& B : cuts[t]->blk) {
         if (B.K == 0) continue;
         char* a = bases[t];
         w += 8.0 * (double)B.K * B.b * B.n;
+        if (B.right()) {  // T = (lam P) Y^+ with Y = conj(Z), into the rebuild's (not yet used) buffer
+          rr.push_back(RightRows{at<double2>(a, B.oU), at<double2>(a, B.oY), at<double2>(a, B.oOut), B.K, B.n, B.b});
+          rmaxK = std::max(rmaxK, B.K);
+          if (mixed) {
+            need = std::max(need, oz_workspace_bytes(B.b, B.K, B.n, false));
+            OzProb q{};
+            q.a = OzOperand{at<double2>(a, B.oP), B.n, 1, nullptr, 1, 0};
+            q.b = OzOperand{at<double2>(a, B.oY), B.n, 1, nullptr, 1, 1};
+            q.M = B.b; q.N = B.K; q.K = B.n; q.C = at<double2>(a, B.oOut); q.ldc = B.K; q.alpha = 1.0;
+            q.s_row = at<double>(a, B.oLam);
+            q.row_div = q.col_div = 1;
+            oz.push_back(q);
+          } else {
+            GemmProb& p = gt.add(B.b, B.K, B.n, at<double2>(a, B.oP), B.n, at<double2>(a, B.oY), B.n,
+                                 at<double2>(a, B.oOut), B.K);
+            p.s_row = at<double>(a, B.oLam);
+          }
+          continue;
+        }
         if (mixed) {
           need = std::max(need, oz_workspace_bytes(B.K, B.n, B.b, false));
           OzProb q{};
@@ -981,12 +1160,29 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
         }
       }
     ProfScope ps(c, TEBD_PROF_PROJECT, w);
+    RightRows* drr = nullptr;
+    if (!rr.empty()) {
+      int err = TEBD_OK;
+      drr = stage(c, rr, &err);
+      if (err) return err;
+      for (size_t y0 = 0; y0 < rr.size(); y0 += 65535) {
+        const unsigned ny = (unsigned)std::min<size_t>(65535, rr.size() - y0);
+        k_right_conj<<<dim3((unsigned)rmaxK, ny), 128, 0, c->stream>>>(drr + y0);
+        c->launches += 1;
+      }
+    }
     if (mixed) {
       if (int r = ensure_ring(c, need)) return r;
       for (size_t j = 0; j < oz.size(); ++j) oz[j].ws = c->u1w->ring[j % OZ_MAXP];
       c->launches += oz_gemm_launch(oz, c->d_status, c->stream);
     } else {
       c->launches += g.launch(c->stream);
+      c->launches += gt.launch(c->stream);
+    }
+    for (size_t y0 = 0; y0 < rr.size(); y0 += 65535) {
+      const unsigned ny = (unsigned)std::min<size_t>(65535, rr.size() - y0);
+      k_right_scale<<<dim3((unsigned)rmaxK, ny), 128, 0, c->stream>>>(drr + y0);
+      c->launches += 1;
     }
     if (int r = check_launch(c)) return r;
   }
@@ -1408,7 +1604,7 @@ int update_chunk_u1_body(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
     }
     if (!ck.ok) return TEBD_ERR_STATE;
     ProfScope ps(c, TEBD_PROF_CONTRACT, wc);
-    if (int r = run_prods(c, pr, 0)) return r;
+    if (int r = launch_gate_blocks(c, pr)) return r;
   }
   // ---- the first cut: pack its blocks from the compact C
   {
@@ -1971,7 +2167,12 @@ int correlators_body(tebd_ctx* h, double2* out) {
   int err = TEBD_OK;
   double* dw = stage(h, wts, &err);
   if (err) return err;
+  // the two products per block: on the FP64 CUDA cores, or (precision 1 and 2) on the
+  // exact-digit engine, whose results carry FP64 accuracy
+  const bool tc = h->precision >= 1;
   Gemm gx(true, OP_C, OP_N), gy(true, OP_N, OP_C);
+  std::vector<OzProb> oz;
+  size_t need = 0;
   std::vector<TraceBlk> tb;
   std::vector<TraceBond> bonds;
   for (size_t i = 0; i < vb.size(); ++i) {
@@ -1982,18 +2183,40 @@ int correlators_body(tebd_ctx* h, double2* out) {
     k_lam2w<<<(X.Kx + 255) / 256, 256, 0, h->stream>>>(at<double>(a, X.oLam), at<double>(a, X.oW), at<double>(a, X.oF),
                                                        X.Kx);
     h->launches += 1;
-    GemmProb& px = gx.add(X.nu, X.nv, X.Kx, at<double2>(a, X.oP), X.nu, at<double2>(a, X.oB), X.nv,
-                          at<double2>(a, X.oX), X.nv);
-    px.s_red = at<double>(a, X.oF);
-    GemmProb& py = gy.add(X.nv, X.nu, X.Ky, at<double2>(a, X.oQ), X.Ky, at<double2>(a, X.oU), X.Ky,
-                          at<double2>(a, X.oY), X.nu);
-    py.s_red = at<double>(a, X.oW) + X.Kx;
+    if (tc) {  // X = P^+ diag(f) B (nu x nv over Kx), Y = Q diag(w) U^+ (nv x nu over Ky)
+      OzProb qx{};
+      qx.a = OzOperand{at<double2>(a, X.oP), 1, X.nu, at<double>(a, X.oF), 1, 1};
+      qx.b = OzOperand{at<double2>(a, X.oB), 1, X.nv, nullptr, 1, 0};
+      qx.M = X.nu; qx.N = X.nv; qx.K = X.Kx; qx.C = at<double2>(a, X.oX); qx.ldc = X.nv; qx.alpha = 1.0;
+      qx.row_div = qx.col_div = 1;
+      OzProb qy{};
+      qy.a = OzOperand{at<double2>(a, X.oQ), X.Ky, 1, at<double>(a, X.oW) + X.Kx, 1, 0};
+      qy.b = OzOperand{at<double2>(a, X.oU), X.Ky, 1, nullptr, 1, 1};
+      qy.M = X.nv; qy.N = X.nu; qy.K = X.Ky; qy.C = at<double2>(a, X.oY); qy.ldc = X.nu; qy.alpha = 1.0;
+      qy.row_div = qy.col_div = 1;
+      need = std::max({need, oz_workspace_bytes(qx.M, qx.N, qx.K, false), oz_workspace_bytes(qy.M, qy.N, qy.K, false)});
+      oz.push_back(qx);
+      oz.push_back(qy);
+    } else {
+      GemmProb& px = gx.add(X.nu, X.nv, X.Kx, at<double2>(a, X.oP), X.nu, at<double2>(a, X.oB), X.nv,
+                            at<double2>(a, X.oX), X.nv);
+      px.s_red = at<double>(a, X.oF);
+      GemmProb& py = gy.add(X.nv, X.nu, X.Ky, at<double2>(a, X.oQ), X.Ky, at<double2>(a, X.oU), X.Ky,
+                            at<double2>(a, X.oY), X.nu);
+      py.s_red = at<double>(a, X.oW) + X.Kx;
+    }
     if (bonds.empty() || bonds.back().out != out + X.k) bonds.push_back(TraceBond{(int)tb.size(), (int)tb.size(), out + X.k});
     tb.push_back(TraceBlk{at<double2>(a, X.oX), at<double2>(a, X.oY), X.nu, X.nv});
     bonds.back().b1 = (int)tb.size();
   }
-  h->launches += gx.launch(h->stream);
-  h->launches += gy.launch(h->stream);
+  if (tc) {
+    if (int r = ensure_ring(h, need)) return r;
+    for (size_t j = 0; j < oz.size(); ++j) oz[j].ws = h->u1w->ring[j % OZ_MAXP];
+    h->launches += oz_gemm_launch(oz, h->d_status, h->stream);
+  } else {
+    h->launches += gx.launch(h->stream);
+    h->launches += gy.launch(h->stream);
+  }
   TraceBlk* dtb = stage(h, tb, &err);
   if (err) return err;
   TraceBond* dbd = stage(h, bonds, &err);

@@ -6,7 +6,12 @@ block, so its Schmidt vectors are a gauge transform of the dense ones:
 observables, sorted spectra, charge multisets and truncation decisions are
 compared, never raw tensors.  Bounds: 1e-9 on densities and currents for the
 FP64 (precision 0) and exact-digit (precision 2) paths, 1e-5 for the mixed
-path (precision 1), 1e-10 on the kept spectra.
+path (precision 1); on the kept spectra 1e-10 after one update and 1e-9 along a
+trajectory.  The Gram route takes each singular value to about eps |theta'|^2 / s
+per update (the Rayleigh values of the Gram's eigenvectors), and over hundreds of
+updates these roundings move the state away from an SVD-based evolution: the
+same route emulated in numpy FP64 on the L = 8 trajectory differs from the
+oracle's spectra by up to 3.9e-10 at t = 1.
 """
 import numpy as np
 import pytest
@@ -33,7 +38,10 @@ def _gpu(wl, precision=0, **kw):
     return TEBD(**_args(wl, **kw), precision=precision, u1=True)
 
 
-def _check_bonds(g, o, spectra_tol=1e-10):
+SPECTRA_TRAJ = 1e-9
+
+
+def _check_bonds(g, o, spectra_tol=SPECTRA_TRAJ):
     """Same chi' on every bond, the same charge multiset and (where chi' agrees) the same
     sorted spectrum; every bond of the GPU state sorted by charge."""
     chi_g, chi_o = list(g.bond_dims()), o.chi()
@@ -194,7 +202,7 @@ def test_u1_synthetic_state_layer(lib):
         n_g, cur_g = g.measure()
         err = max(np.max(np.abs(n_g - o.densities())), np.max(np.abs(cur_g - o.currents())))
         assert err < TOL, (residue, err)
-        assert not _check_bonds(g, o)
+        assert not _check_bonds(g, o, 1e-10)
     # B_{i+2} = V2^+ of every triple of the last layer has orthonormal rows (a synthetic state's
     # lambdas are not the Schmidt values of its tensors, so its canonical densities need not sum to N)
     from state_checks import canonical_error
