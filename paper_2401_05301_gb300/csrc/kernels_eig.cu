@@ -556,6 +556,15 @@ constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian pro
 // squares, in empty regions of the chain, and once subnormal the scale 1/amax of
 // the reflector would overflow and turn the column into NaN.
 constexpr double REFL_FLUSH = 0x1p-900;
+// The last TD_TAIL or fewer columns of every matrix are reduced by one block per
+// matrix with the trailing matrix in shared memory (k_tridiag_tail): there the
+// cooperative kernel would pay three grid barriers per column for very little work.
+// A matrix takes part in the panels k0 < tail_start(m) (a multiple of TD_NB), so the
+// split depends on its own size only and each result is independent of its batch.
+constexpr int TD_TAIL = 64;
+__host__ __device__ __forceinline__ int tail_start(int m) {
+  return m <= TD_TAIL ? 0 : ((m - TD_TAIL + TD_NB - 1) / TD_NB) * TD_NB;
+}
 
 
 // Grid barrier for a cooperative launch.  st = {arrival count, unused, error}.
@@ -811,7 +820,7 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
     for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
       const EigMat& M = b.a[mi];
       const int m = M.m;
-      if (k >= m) continue;
+      if (k >= tail_start(m)) continue;
       if (m - k <= P1_R * (int)blockDim.x) {
         phase1_regs(M, k, j, red_sh, &scale_sh);
         continue;
@@ -846,7 +855,7 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
     for (int item = blockIdx.x;; item += gridDim.x) {
       int rem = item, mi = -1;
       for (int i = 0; i < b.n; ++i) {
-        const int n = b.a[i].m - k - 1;
+        const int n = (k < tail_start(b.a[i].m)) ? b.a[i].m - k - 1 : 0;
         const int ni = (n > 0) ? ((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK) : 0;
         if (rem < ni) { mi = i; break; }
         rem -= ni;
@@ -917,7 +926,7 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
     for (int item = blockIdx.x;; item += gridDim.x) {
       int rem = item, mi = -1;
       for (int i = 0; i < b.n; ++i) {
-        const int n = b.a[i].m - k - 1;
+        const int n = (k < tail_start(b.a[i].m)) ? b.a[i].m - k - 1 : 0;
         const int ns = (n > 0) ? (n + TD_STRIP - 1) / TD_STRIP : 0;
         if (rem < ns) { mi = i; break; }
         rem -= ns;
@@ -991,7 +1000,126 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
   // w of the panel's last column
   for (int mi = blockIdx.x; mi < b.n; mi += gridDim.x) {
     const EigMat& M = b.a[mi];
-    if (k1 - 1 < M.m - 1) finish_w(M, k1 - 1, k1 - 1 - k0, rank2_alpha(M, k1 - 1, M.m - k1));
+    if (k0 < tail_start(M.m) && k1 - 1 < M.m - 1) finish_w(M, k1 - 1, k1 - 1 - k0, rank2_alpha(M, k1 - 1, M.m - k1));
+  }
+}
+
+// The columns [tail_start(m), m) of one matrix per block, unblocked, with the
+// trailing matrix (n <= TD_TAIL, current when the kernel starts) in shared memory
+// as a full Hermitian matrix.  The reflectors are those of the panel kernel
+// (phase1_regs' arithmetic on the pivot row), stored the same way in the rows of H;
+// each column then applies A <- A - v w^+ - w v^+ with p = tau A v,
+// w = p - (tau (p^+ v) / 2) v.  One fixed order per reduction.
+constexpr int TL_LD = TD_TAIL + 1;
+__global__ void __launch_bounds__(256) k_tridiag_tail(const __grid_constant__ EigBatch b) {
+  extern __shared__ double2 tl_sh[];
+  double2* As = tl_sh;                      // TD_TAIL x TL_LD
+  double2* vs = As + TD_TAIL * TL_LD;       // v of the current column
+  double2* ws = vs + TD_TAIL;               // p, then w
+  __shared__ double red_sh[33];
+  __shared__ double2 sc_sh, alpha_sh;
+  const EigMat& M = b.a[blockIdx.x];
+  const int m = M.m, k0 = tail_start(m), nt = m - k0;
+  if (nt <= 0) return;
+  for (int e = threadIdx.x; e < nt * nt; e += blockDim.x) {
+    const int r = e / nt, c = e % nt;
+    if (c >= r) {
+      const double2 x = M.H[(size_t)(k0 + r) * m + k0 + c];
+      As[r * TL_LD + c] = x;
+      As[c * TL_LD + r] = cconj(x);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < nt; ++j) {
+    const int k = k0 + j, nn = nt - j;  // row j of the current matrix from its diagonal: nn entries
+    const double2* row = As + j * TL_LD + j;
+    if (nn == 1) {
+      if (threadIdx.x == 0) {
+        M.d[k] = row[0].x;
+        M.e[k] = 0.0;
+        M.tau[k] = make_double2(0.0, 0.0);
+        M.H[(size_t)k * m + k] = row[0];
+      }
+      break;
+    }
+    double amax = 0.0;
+    for (int r = 1 + threadIdx.x; r < nn; r += blockDim.x) amax = fmax(amax, fmax(fabs(row[r].x), fabs(row[r].y)));
+    amax = -block_min(-amax, red_sh);
+    if (amax < REFL_FLUSH) amax = 0.0;
+    const double sinv = (amax > 0.0) ? 1.0 / amax : 0.0;
+    double s2 = 0.0;
+    for (int r = 2 + threadIdx.x; r < nn; r += blockDim.x) {
+      const double vx = row[r].x * sinv, vy = row[r].y * sinv;
+      s2 = fma(vx, vx, fma(vy, vy, s2));
+    }
+    const double xnorm2 = block_sum(s2, red_sh);
+    if (threadIdx.x == 0) {
+      const double2 x0 = row[1];
+      const double ar = x0.x * sinv, ai = -x0.y * sinv;
+      double beta;
+      double2 tau, sc;
+      if (amax == 0.0 || (xnorm2 == 0.0 && ai == 0.0)) {
+        beta = x0.x;
+        tau = make_double2(0.0, 0.0);
+        sc = make_double2(0.0, 0.0);
+      } else {
+        const double bs = -copysign(sqrt(ar * ar + ai * ai + xnorm2), ar);
+        tau = make_double2((bs - ar) / bs, -ai / bs);
+        const double zr = ar - bs, zi = ai, den = zr * zr + zi * zi;
+        sc = make_double2(zr / den * sinv, -zi / den * sinv);
+        beta = bs * amax;
+      }
+      M.d[k] = row[0].x;
+      M.e[k] = beta;
+      M.tau[k] = tau;
+      M.H[(size_t)k * m + k] = row[0];
+      sc_sh = sc;
+    }
+    __syncthreads();
+    const double2 sc = sc_sh, tau = M.tau[k];
+    const int n = nn - 1;  // trailing indices r = 0..n-1 <-> rows/columns j+1+r
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      const double2 v = (r == 0) ? make_double2(1.0, 0.0) : cmul(cconj(row[1 + r]), sc);
+      vs[r] = v;
+      M.H[(size_t)k * m + k + 1 + r] = v;
+    }
+    __syncthreads();
+    // p = tau A v over the trailing block, four threads per row
+    const double2* At = As + (j + 1) * TL_LD + (j + 1);
+    {
+      const int r = threadIdx.x >> 2, part = threadIdx.x & 3;
+      double2 acc = make_double2(0.0, 0.0);
+      if (r < n)
+        for (int c = part; c < n; c += 4) acc = cfma(At[r * TL_LD + c], vs[c], acc);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (part == 0 && r < n) ws[r] = cmul(tau, acc);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // alpha = -tau (p^+ v) / 2
+      double2 dot = make_double2(0.0, 0.0);
+      for (int r = threadIdx.x; r < n; r += 32) dot = cfma_conj(ws[r], vs[r], dot);
+      dot = warp_sum2(dot);
+      if (threadIdx.x == 0) {
+        const double2 t2 = cmul(tau, dot);
+        alpha_sh = make_double2(-0.5 * t2.x, -0.5 * t2.y);
+      }
+    }
+    __syncthreads();
+    const double2 alpha = alpha_sh;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) ws[r] = cfma(alpha, vs[r], ws[r]);
+    __syncthreads();
+    double2* Aw = As + (j + 1) * TL_LD + (j + 1);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e % n;
+      double2 a = Aw[r * TL_LD + c];
+      a = csub(a, cmul(vs[r], cconj(ws[c])));
+      a = csub(a, cmul(ws[r], cconj(vs[c])));
+      Aw[r * TL_LD + c] = a;
+    }
+    __syncthreads();
   }
 }
 
@@ -1023,16 +1151,21 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
     grid = std::max(1, sms * std::min(per_sm, 3));
   }
   int launches = 0;
-  for (int k0 = 0; k0 < mm; k0 += TD_NB) {
+  int kend = 0;  // panels run while any matrix has columns before its tail
+  for (int i = 0; i < b.n; ++i) kend = std::max(kend, tail_start(b.a[i].m));
+  for (int k0 = 0; k0 < kend; k0 += TD_NB) {
     int k1 = std::min(mm, k0 + TD_NB);
     // grid sized to the panel's largest phase (its first column's slabs): small matrices
-    // get a small grid, whose barriers are cheaper; at least one block per matrix
+    // get a small grid, whose barriers are cheaper; at least one block per active matrix
     long long items = 0;
+    int active = 0;
     for (int i = 0; i < b.n; ++i) {
+      if (k0 >= tail_start(b.a[i].m)) continue;
+      ++active;
       const int n = b.a[i].m - k0 - 1;
       if (n > 0) items += (long long)((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK);
     }
-    const int gsz = (int)std::min<long long>(grid, std::max<long long>(b.n, items));
+    const int gsz = (int)std::min<long long>(grid, std::max<long long>(active, items));
     cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
     void* args[] = {const_cast<EigBatch*>(&b), &k0, &k1};
     if (cudaLaunchCooperativeKernel((const void*)k_tridiag_panel, dim3(gsz), dim3(TD_THREADS), args, 0, s) !=
@@ -1045,7 +1178,7 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
     for (int i = 0; i < b.n; ++i) {
       const EigMat& M = b.a[i];
       const int n = M.m - k1;
-      if (n <= 0) continue;
+      if (n <= 0 || k0 >= tail_start(M.m)) continue;
       double2* C = M.H + (size_t)k1 * M.m + k1;
       const double2* VW = M.pan + (size_t)k1 * 2 * TD_NB;
       const double2* WV = M.pan + (size_t)M.m * 2 * TD_NB + (size_t)k1 * 2 * TD_NB;
@@ -1071,6 +1204,16 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
       }
     }
     launches += mixed ? oz_gemm_launch(oz, status, s) : g.launch(s);
+  }
+  {
+    constexpr int TL_SMEM = (TD_TAIL * TL_LD + 2 * TD_TAIL) * (int)sizeof(double2);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_tridiag_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, TL_SMEM);
+      attr = true;
+    }
+    k_tridiag_tail<<<b.n, 256, TL_SMEM, s>>>(b);
+    ++launches;
   }
   k_esq<<<dim3(std::max(1, std::min(64, (mm + 255) / 256)), b.n), 256, 0, s>>>(b);
   return launches + 1;
