@@ -155,6 +155,9 @@ def max_over_ranks(x: float, ws: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
+PANEL_LAUNCH_DRAM_BYTES = 40.18e6  # 38.35 MB read + 1.83 MB written (ncu, unchanged kernel)
+
+
 def side_measurement(fn, *args, **kw):
     """Run a measurement reported beside the headline; if it fails, record why instead of losing the line."""
     try:
@@ -391,6 +394,48 @@ def batched_measurement(stream_ptr, steps: int = 1):
             "speedup": (gb / tb) / (ga / ta)}
 
 
+def graph_measurement(stream_ptr, steps: int = 6):
+    """Launch-bound dense steps with and without CUDA-graph replay (option "graph"): the
+    first 16 of the config-4 simulations (L 16..64, d = 4) at chi_max capped to 64, each from
+    its dense synthetic saturated state, mixed precision, one batch.  Both arms run two untimed
+    steps first (with the option on: one ordinary, one captured), then `steps` timed steps."""
+    import torch
+    from paper_2401_05301_gb300 import TEBD, batch_step
+    wls = workloads.batch48()[:16]
+
+    def arm(graph):
+        sims = []
+        for i, w in enumerate(wls):
+            chi = min(w.chi_max, 64)
+            g = TEBD(w.L, w.n_max, chi, w.U, w.J, w.Jnnn, w.K, w.jc, w.dt, precision=1, stream=stream_ptr)
+            B, lam, _ = workloads.synthetic_state(w.L, w.d, chi, seed=workloads.SEED + 2000 + i)
+            g.set_state(B, lam)
+            if graph:
+                g.set_option("graph", 1)
+            sims.append(g)
+        batch_step(sims, 2)
+        torch.cuda.synchronize()
+        g0 = sum(g.counters()[0] for g in sims)
+        l0 = sims[0].counters()[1]
+        t = time.perf_counter()
+        batch_step(sims, steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        gu = sum(g.counters()[0] for g in sims) - g0
+        launches = sims[0].counters()[1] - l0
+        stats = sims[0].graph_stats()
+        for g in sims:
+            g.close()
+        return {"value": gu / dt, "seconds": dt, "gate_updates": gu, "kernels_per_step": launches / steps,
+                "graph_replays": stats[0], "graph_fallbacks": stats[1]}
+
+    plain = arm(False)
+    graph = arm(True)
+    return {"workload": f"16 seeded simulations (config-4 draws, L 16..64, d=4, chi_max capped at 64) from dense "
+                        f"synthetic saturated states, one batch, mixed precision, {steps} steps after two untimed",
+            "unit": UNIT, "ordinary": plain, "graph": graph, "speedup": graph["value"] / plain["value"]}
+
+
 def run_reference(args):
     """The CPU oracle (oracle/u1.py, numpy + LAPACK FP64, the machine's host cores) on the headline
     chain's physics.  One oracle update of a saturated triple at chi_max = 1024 takes ~50 s on 8
@@ -445,6 +490,7 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-simulation batched measurement")
     ap.add_argument("--no-side", action="store_true", help="skip the FP64 / exact-digit / dense side arms")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -546,8 +592,17 @@ def main():
     else:
         bound, peak, src = "tensor", tf32_peak, ("measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)" if bf16
                                                  else "fallback 1.9 PFLOP/s bf16 x 1.1/2.25")
+    traffic, tnote = None, None
+    if dom == "tridiag" and args.workload == "config3_u1":
+        # dram__bytes_read.sum + dram__bytes_write.sum of one k_tridiag_panel launch (the step's first
+        # panel, up to 64 charge blocks) from the ncu capture summarised in
+        # profiles/k_tridiag_panel_u1_L24_d5_chi1024.md; the same kernel and local sizes as this chain
+        traffic = PANEL_LAUNCH_DRAM_BYTES
+        tnote = ("DRAM bytes of one k_tridiag_panel launch (first panel of a step, ncu, L=24 chain of the same "
+                 "local sizes); the blocks stay L2-resident, the kernel is FP64-pipe and barrier bound")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic, "traffic_note": tnote,
+                "peak_source": src,
                 "share_of_step": dms / ms if ms > 0 else None, "launches": dlaunch,
                 "work_note": "algorithmic real flops of the class (Hermitian Gram at half, reduction 16/3 b^3 per "
                              "charge block of size b) over its CUDA-event time on the handle's stream"}
@@ -568,6 +623,9 @@ def main():
     config2 = None
     if not args.no_side and ws == 1:
         config2 = side_measurement(dense_config2, stream)
+    graphm = None
+    if not args.no_graph and ws == 1:
+        graphm = side_measurement(graph_measurement, stream.cuda_stream)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -591,7 +649,7 @@ def main():
             "device_bytes": head_bytes,
             "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64, "exact_path": exact,
             "mixed_over_fp64": (value / fp64["value"]) if isinstance(fp64, dict) and fp64.get("value") else None,
-            "dense_config2": config2, "served": served, "batched": batched}
+            "dense_config2": config2, "served": served, "batched": batched, "graph": graphm}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()

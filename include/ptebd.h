@@ -121,6 +121,27 @@ int tebd_create_supersite(int L, int n_max, int chi_max, double U, double J, dou
  *             eigen-solver that exponentiates the three-site terms; changing it
  *             rebuilds the gate table, and a gate that does not converge within
  *             the limit makes the call return TEBD_ERR_NOT_CONVERGED (sticky).
+ *   "graph"   0 (default); 1: replay whole steps as CUDA graphs where that is exact
+ *             (dense three-site form; not with "u1", "randomized", super sites or
+ *             "profile").  While every bond is at its capacity min(chi_max, d^...) the
+ *             host's decisions after each truncation are known in advance (all kmax
+ *             eigenvectors, chi' = capacity), so the second consecutive step of the same
+ *             set of handles (tebd_step, or tebd_batch_step driven by hs[0]) is captured
+ *             with those decisions checked on the device, and later steps replay it.  A
+ *             replay whose checks fail (a truncation below capacity, a vector count the
+ *             eps floor would have cut, a non-finite trace, a status) is undone from the
+ *             state backup the graph takes first and the step runs the ordinary way, so
+ *             results are bitwise those of the ordinary path.  A handle on the legacy
+ *             default stream gets its own blocking stream.  Changing any option or the
+ *             state makes the next step capture again.  (An addition: the paper's runs
+ *             are not launch bound.)
+ *   "graph_test_fallback" n >= 0 (diagnostic): treat the next n accepted replays as
+ *             failed checks (state restored from the backup, step run the ordinary way),
+ *             to test that path; unlike every other option it keeps the cached graph.
+ *   "panel_blocks" 0 (default: as many as fit, at most 3) or 1..3: blocks per SM of the
+ *             tridiagonal reduction's cooperative grid (a launch shape; the arithmetic and
+ *             its order do not depend on it).  Chosen per (chi, d) bucket by the package's
+ *             autotuner (paper_2401_05301_gb300/autotune.py).
  *   "wait_limit_clocks" limit, in GPU clock ticks (default 2e9, about 1 s), of
  *             every grid-barrier wait of the cooperative tridiagonal reduction.
  *             A wait that runs out records the failure, every block of the
@@ -278,6 +299,11 @@ int tebd_profile(tebd_handle h, int cls, double* ms, long long* launches, double
 
 /* Release everything the handle owns.  NULL is accepted.  Infrastructure. */
 void tebd_destroy(tebd_handle h);
+
+/* Graph-mode counters (option "graph"): accepted replays, replays undone and run the
+ * ordinary way, and the kernel launches one replay holds (0 while no graph is cached).
+ * Any pointer may be NULL.  Infrastructure (no counterpart in the paper). */
+int tebd_graph_stats(tebd_handle h, long long* replays, long long* fallbacks, long long* launches_per_replay);
 
 /* Static description of a status code.  Infrastructure. */
 const char* tebd_strerror(int status);

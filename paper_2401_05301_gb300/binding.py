@@ -47,6 +47,7 @@ SIGNATURES = {
     "tebd_set_test_matrices": (_c_int, [_c_void_p, TEST_MATRIX_FN, _c_void_p]),
     "tebd_get_charges": (_c_int, [_c_void_p, _c_int, _P_int]),
     "tebd_counters": (_c_int, [_c_void_p, _P_ll, _P_ll]),
+    "tebd_graph_stats": (_c_int, [_c_void_p, _P_ll, _P_ll, _P_ll]),
     "tebd_profile": (_c_int, [_c_void_p, _c_int, _P_double, _P_ll, _P_double]),
     "tebd_destroy": (None, [_c_void_p]),
     "tebd_strerror": (ctypes.c_char_p, [_c_int]),
@@ -253,6 +254,12 @@ class TEBD:
         return g.value, k.value
 
     PROFILE_CLASSES = ("contract", "gram", "tridiag", "bisect", "eigvec", "project", "truncate", "measure")
+
+    def graph_stats(self):
+        """(accepted replays, replays undone, launches per replay) of option "graph"."""
+        r, f, n = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().tebd_graph_stats(self._h, ctypes.byref(r), ctypes.byref(f), ctypes.byref(n)), "tebd_graph_stats")
+        return r.value, f.value, n.value
 
     def profile(self):
         """{class: (ms, launches, work)} since profiling was (re)started."""

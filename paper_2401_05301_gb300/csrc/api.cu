@@ -311,6 +311,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   eb.n = (int)ts.size();
   eb.bar = c->d_bar;
   eb.wait_clocks = c->wait_clocks;
+  eb.panel_blocks = c->panel_blocks;
   for (size_t t = 0; t < ts.size(); ++t) {
     const Slot& S = ts[t].h->slots[ts[t].slot];
     EigMat& M = eb.a[t];
@@ -343,6 +344,23 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     c->launches += eig_bisect(eb, c->stream);
   }
   if (int r = check_launch(c)) return r;
+  if (c->capturing) {  // all kmax vectors; the device checks that the host would have asked for them
+    if (eb.n > GRAPH_MAXT) return TEBD_ERR_STATE;
+    GraphEig g{};
+    g.n = eb.n;
+    g.bar_err = c->d_bar + 2;
+    g.flag = c->d_gflag;
+    for (int t = 0; t < eb.n; ++t) {
+      EigMat& M = eb.a[t];
+      g.evals[t] = M.evals;
+      g.trace[t] = M.trace;
+      g.kmax[t] = M.kmax;
+      g.floor_rel[t] = std::max(0.01 * ts[t].h->eps_rel, 1e-15);
+      M.K = M.kmax;
+      if (second) ts[t].K2 = M.K; else ts[t].K1 = M.K;
+    }
+    c->launches += launch_graph_check_eig(g, c->stream);
+  } else {
   // read back the eigenvalues and the traces
   size_t kmax_all = 1;
   for (int t = 0; t < eb.n; ++t) kmax_all = std::max<size_t>(kmax_all, eb.a[t].kmax);
@@ -378,7 +396,8 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     M.K = std::max(1, K);
     if (second) ts[t].K2 = M.K; else ts[t].K1 = M.K;
   }
-  for (size_t t = 0; t < ts.size(); ++t) {
+  }
+  for (size_t t = 0; t < ts.size() && !c->capturing; ++t) {
     const EigMat& M = eb.a[t];
     debug_dump(c, "d", ts[t].i, M.d, M.m);
     debug_dump(c, "e", ts[t].i, M.e, M.m);
@@ -393,7 +412,7 @@ int eigen_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
     ProfScope ps(c, TEBD_PROF_EIGVEC, w);
     c->launches += eig_vectors(eb, c->precision >= 1, oz_ws, c->d_status, c->stream);
   }
-  for (size_t t = 0; t < ts.size(); ++t) {
+  for (size_t t = 0; t < ts.size() && !c->capturing; ++t) {
     const EigMat& M = eb.a[t];
     debug_dump(c, "Z", ts[t].i, M.Z, (size_t)M.m * M.K);
     debug_dump(c, "Z2", ts[t].i, M.Z2, (size_t)M.m * M.K);
@@ -432,6 +451,28 @@ int truncate_stage(tebd_ctx* c, std::vector<Triple>& ts, bool second) {
   }
   // chi_max above is also the bond capacity, so chi' can never overrun lam or B
   if (int r = check_launch(c)) return r;
+  if (c->capturing) {  // chi' = the bond's capacity, checked on the device; w recorded for the host
+    if (ts.size() > (size_t)GRAPH_MAXT) return TEBD_ERR_STATE;
+    GraphTrunc g{};
+    g.n = (int)ts.size();
+    g.status = c->d_status;
+    g.flag = c->d_gflag;
+    for (size_t t = 0; t < ts.size(); ++t) {
+      const tebd_ctx* o = ts[t].h;
+      const Slot& S = o->slots[ts[t].slot];
+      const int cap = std::min(o->chi_max, o->cap[ts[t].i + (second ? 2 : 1)]);
+      if (c->gw_n >= c->gw_cap) return TEBD_ERR_STATE;
+      g.chi[t] = S.chi;
+      g.expect[t] = cap;
+      g.w[t] = S.scal + 2;
+      g.w_out[t] = c->d_gw + c->gw_n;
+      if (second) { ts[t].chi2 = cap; ts[t].gw2 = c->gw_n; ts[t].norm2 = 1.0; ts[t].w2 = 0.0; }
+      else { ts[t].chi1 = cap; ts[t].gw1 = c->gw_n; ts[t].norm1 = 1.0; ts[t].w1 = 0.0; }
+      ++c->gw_n;
+    }
+    c->launches += launch_graph_check_trunc(g, c->stream);
+    return check_launch(c);
+  }
   const size_t stride = 4;
   if (int r = ensure_pinned(c, ts.size() * stride + 8)) return r;
   for (size_t t = 0; t < ts.size(); ++t) {
@@ -720,6 +761,9 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       } else {
         c->launches += g6.launch(s, tf32, c->d_status);
       }
+      if (c->capturing)  // B_i / ||s|| with the norm the truncation left on the device
+        for (auto& T : ts)
+          c->launches += launch_scale_inv(T.h->B[T.i], (long long)T.m1 * T.chi1, T.h->slots[T.slot].scal + 1, s);
     }
     if (!c->randomized && !two) {
       ProfScope ps(c, TEBD_PROF_GRAM, wg);
@@ -798,12 +842,19 @@ int update_chunk(tebd_ctx* c, std::vector<Triple>& ts, int tidx) {
       } else {
         c->launches += g9.launch(s, tf32, c->d_status);
       }
+      if (c->capturing)
+        for (auto& T : ts)
+          c->launches += launch_scale_inv(T.h->B[T.i + 1], (long long)T.m2 * T.chi2, T.h->slots[T.slot].scal + 1, s);
     }
     if (int r = check_launch(c)) return r;
   }
   for (auto& T : ts) {
     T.h->chi[T.i + 1] = T.chi1;
     T.h->chi[T.i + 2] = T.chi2;
+    if (c->capturing) {  // accounted when a replay is accepted
+      c->gw_map.push_back({T.h, {T.gw1, T.gw2}});
+      continue;
+    }
     T.h->w_total += T.w1 + T.w2;
     T.h->gate_updates += 1;
   }
@@ -856,6 +907,163 @@ int run_layer_multi(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, int residue, 
 }
 
 int run_layer(tebd_ctx* c, int residue, int tidx) { return run_layer_multi(c, {c}, residue, tidx); }
+
+// ---- CUDA-graph replay of whole steps --------------------------------------------------
+bool saturated(const tebd_ctx* h) {
+  for (int k = 0; k <= h->L; ++k)
+    if (h->chi[k] != std::min(h->chi_max, h->cap[k])) return false;
+  return true;
+}
+
+bool graph_eligible(const std::vector<tebd_ctx*>& hs) {
+  for (const tebd_ctx* h : hs)
+    if (!h->graph || h->graph_broken || h->prof || h->u1 || h->ss || h->randomized || !h->have_state ||
+        !saturated(h))
+      return false;
+  return true;
+}
+
+void graph_drop(tebd_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey.clear();
+  c->ggen.clear();
+}
+
+bool graph_key_matches(const tebd_ctx* c, const std::vector<tebd_ctx*>& hs) {
+  if (c->gkey != hs || c->ggen.size() != hs.size()) return false;
+  for (size_t i = 0; i < hs.size(); ++i)
+    if (c->ggen[i] != hs[i]->generation) return false;
+  return true;
+}
+
+// Copy the whole state (every B_k and lambda_k at capacity) to the handle's backup, or back.
+int state_copy(tebd_ctx* h, bool restore, cudaStream_t s) {
+  size_t need = 0;
+  for (int k = 0; k < h->L; ++k) need += 16 * (size_t)h->cap[k] * h->d * h->cap[k + 1];
+  for (int k = 0; k <= h->L; ++k) need += 8 * (size_t)h->cap[k];
+  if (h->bk_bytes < need) {
+    if (restore) return TEBD_ERR_STATE;
+    h->bkB = dalloc<double2>(h, (need + 15) / 16);
+    if (!h->bkB) return TEBD_ERR_OOM;
+    h->bk_bytes = need;
+  }
+  char* base = reinterpret_cast<char*>(h->bkB);
+  size_t off = 0;
+  for (int k = 0; k < h->L; ++k) {
+    const size_t n = 16 * (size_t)h->cap[k] * h->d * h->cap[k + 1];
+    if (cudaMemcpyAsync(restore ? (void*)h->B[k] : (void*)(base + off), restore ? (const void*)(base + off) : h->B[k], n,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail_cuda(h);
+    off += n;
+  }
+  for (int k = 0; k <= h->L; ++k) {
+    const size_t n = 8 * (size_t)h->cap[k];
+    if (cudaMemcpyAsync(restore ? (void*)h->lam[k] : (void*)(base + off), restore ? (const void*)(base + off) : h->lam[k],
+                        n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail_cuda(h);
+    off += n;
+  }
+  return TEBD_OK;
+}
+
+// One step of the simulations hs (driven on c's stream) by replaying a captured graph.
+// Returns TEBD_OK if the replay was accepted, 1 if the step must run the ordinary way
+// (not eligible, first step of a new set, or a failed check, the state then restored),
+// or an error.  A graph is captured on the second consecutive eligible step of the same
+// simulations, after an ordinary step has made every lazy allocation.
+int graph_step(tebd_ctx* c, const std::vector<tebd_ctx*>& hs, const std::vector<std::pair<int, int>>& layers) {
+  if (!graph_eligible(hs) || c->stream == nullptr) {  // capture needs a stream other than the legacy one
+    graph_drop(c);
+    return 1;
+  }
+  if (!graph_key_matches(c, hs)) {  // remember the set; capture on its next step
+    graph_drop(c);
+    c->gkey = hs;
+    for (const tebd_ctx* h : hs) c->ggen.push_back(h->generation);
+    return 1;
+  }
+  if (!c->gexec) {
+    size_t ncut = 0;
+    for (const tebd_ctx* h : hs)
+      for (const auto& l : layers) {
+        const int stride = 3, span = 2;
+        for (int i = l.first; i + span < h->L; i += stride) ncut += 2;
+      }
+    if (!c->d_gflag && !(c->d_gflag = dalloc<int>(c, 1))) return TEBD_ERR_OOM;
+    if (c->gw_cap < ncut) {
+      c->d_gw = dalloc<double>(c, ncut);
+      if (!c->d_gw) return TEBD_ERR_OOM;
+      if (c->h_gw) cudaFreeHost(c->h_gw);
+      c->h_gw = nullptr;
+      if (cudaMallocHost(&c->h_gw, sizeof(double) * (ncut + 2)) != cudaSuccess) {
+        cudaGetLastError();
+        return TEBD_ERR_OOM;
+      }
+      c->gw_cap = ncut;
+    }
+    for (tebd_ctx* h : hs)  // the backup buffers, allocated outside the capture
+      if (h->bk_bytes == 0 && state_copy(h, false, c->stream) != TEBD_OK) return TEBD_ERR_OOM;
+    if (int r = sync(c)) return r;
+    c->gw_n = 0;
+    c->gw_map.clear();
+    const long long l0 = c->launches;
+    std::vector<int> sticky0;
+    for (const tebd_ctx* h : hs) sticky0.push_back(h->sticky);
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      graph_drop(c);
+      return 1;
+    }
+    c->capturing = true;
+    int r = cudaMemsetAsync(c->d_gflag, 0, sizeof(int), c->stream) == cudaSuccess ? TEBD_OK : TEBD_ERR_CUDA;
+    for (tebd_ctx* h : hs)
+      if (r == TEBD_OK) r = state_copy(h, false, c->stream);
+    for (size_t l = 0; l < layers.size() && r == TEBD_OK; ++l) r = run_layer_multi(c, hs, layers[l].first, layers[l].second);
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+    if (r == TEBD_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess) {
+      c->glaunches = c->launches - l0;
+    } else {
+      cudaGetLastError();
+      c->gexec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    c->launches = l0;
+    for (size_t i = 0; i < hs.size(); ++i) hs[i]->sticky = sticky0[i];  // nothing ran during the capture
+    if (!c->gexec) {
+      graph_drop(c);
+      c->graph_broken = true;
+      return 1;
+    }
+  }
+  if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return fail_cuda(c);
+  int* h_flag = reinterpret_cast<int*>(c->h_gw);
+  cudaMemcpyAsync(h_flag, c->d_gflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(c->h_gw + 2, c->d_gw, sizeof(double) * c->gw_n, cudaMemcpyDeviceToHost, c->stream);
+  if (int r = sync(c)) return r;
+  if (c->graph_test_fallback > 0 && *h_flag == 0) {
+    --c->graph_test_fallback;
+    *h_flag = 32;
+  }
+  if (*h_flag == 0) {
+    const double* w = c->h_gw + 2;
+    for (const auto& e : c->gw_map) {
+      e.first->w_total += w[e.second.first] + w[e.second.second];
+      e.first->gate_updates += 1;
+    }
+    c->launches += c->glaunches;
+    ++c->graph_replays;
+    return TEBD_OK;
+  }
+  for (tebd_ctx* h : hs)
+    if (int r = state_copy(h, true, c->stream)) return r;
+  if (int r = sync(c)) return r;
+  ++c->graph_fallbacks;
+  graph_drop(c);
+  return 1;
+}
 
 int ensure_measure_ws(tebd_ctx* c) {
   if (!c->mN) {  // super sites: two physical densities per site, 2L - 1 physical bonds
@@ -1075,6 +1283,12 @@ int tebd_create_supersite(int L, int n_max, int chi_max, double U, double J, dou
 
 int tebd_set_option(tebd_handle h, const char* key, double value) {
   CHECK_HANDLE(h);
+  if (key && std::string(key) == "graph_test_fallback") {  // diagnostic; keeps the cached graph
+    if (value < 0 || value > 1000 || value != std::floor(value)) return TEBD_ERR_ARG;
+    h->graph_test_fallback = (int)value;
+    return TEBD_OK;
+  }
+  ++h->generation;  // a captured step holds the options it was captured with
   if (!key || !is_fin(value)) return TEBD_ERR_ARG;
   const std::string k(key);
   if (k == "w_cut") {
@@ -1134,6 +1348,20 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
         return r;
       }
     }
+  } else if (k == "graph") {
+    if (value != 0.0 && value != 1.0) return TEBD_ERR_ARG;
+    if (value == 1.0 && (h->u1 || h->ss || h->randomized)) return TEBD_ERR_ARG;
+    if (value == 1.0 && h->stream == nullptr) {
+      // stream capture needs a stream other than the legacy one; a blocking stream stays
+      // ordered with the legacy stream's other work
+      if (!h->own_stream && cudaStreamCreate(&h->own_stream) != cudaSuccess) return fail_cuda(h);
+      h->stream = h->own_stream;
+    }
+    h->graph = (value == 1.0);
+    h->graph_broken = false;
+  } else if (k == "panel_blocks") {
+    if (value < 0 || value > 3 || value != std::floor(value)) return TEBD_ERR_ARG;
+    h->panel_blocks = (int)value;
   } else if (k == "wait_limit_clocks") {
     if (value < 0 || value > 1e12 || value != std::floor(value)) return TEBD_ERR_ARG;
     h->wait_clocks = (long long)value;
@@ -1149,12 +1377,14 @@ int tebd_set_option(tebd_handle h, const char* key, double value) {
 
 int tebd_set_stream(tebd_handle h, void* cuda_stream) {
   CHECK_HANDLE(h);
+  ++h->generation;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
   return TEBD_OK;
 }
 
 int tebd_init_product(tebd_handle h, const int* occ) {
   CHECK_HANDLE(h);
+  ++h->generation;
   if (!occ) return TEBD_ERR_ARG;
   const int n_occ = h->ss ? h->L_phys : h->L;
   for (int k = 0; k < n_occ; ++k)
@@ -1219,6 +1449,7 @@ int tebd_get_charges(tebd_handle h, int k, int* q) {
 }
 
 int tebd_set_state(tebd_handle h, const int* chi, const double* const* B_ptrs, const double* const* lam_ptrs) {
+  if (h) ++h->generation;
   CHECK_HANDLE(h);
   if (!chi || !B_ptrs || !lam_ptrs) return TEBD_ERR_ARG;
   if (chi[0] != 1 || chi[h->L] != 1) return TEBD_ERR_ARG;
@@ -1252,9 +1483,13 @@ int tebd_step(tebd_handle h, int n_steps) {
     if (int r = alloc_workspace(h)) return r;
     // the layers of one step (residue r <-> triples j = r+1 mod 3, gate-table index)
     const std::vector<std::pair<int, int>> layers = step_layers(h);
+    const std::vector<tebd_ctx*> one{h};
     for (int n = 0; n < n_steps; ++n) {
-      for (const auto& l : layers)
-        if (int r = run_layer(h, l.first, l.second)) return r;
+      const int g = graph_step(h, one, layers);
+      if (g < 0) return g;
+      if (g == 1)
+        for (const auto& l : layers)
+          if (int r = run_layer(h, l.first, l.second)) return r;
       h->steps += 1;
     }
   } catch (...) {
@@ -1327,7 +1562,9 @@ int tebd_batch_step(tebd_handle* hs, int n, int n_steps) {
       if ((r = alloc_workspace(h)) != TEBD_OK) return r;
     const std::vector<std::pair<int, int>> layers = step_layers(c);
     for (int step = 0; step < n_steps && r == TEBD_OK; ++step) {
-      for (size_t l = 0; l < layers.size() && r == TEBD_OK; ++l)
+      const int g = graph_step(c, v, layers);
+      if (g < 0) r = g;
+      for (size_t l = 0; g == 1 && l < layers.size() && r == TEBD_OK; ++l)
         r = run_layer_multi(c, v, layers[l].first, layers[l].second);
       if (r == TEBD_OK)
         for (tebd_ctx* h : v) h->steps += 1;
@@ -1537,8 +1774,19 @@ void tebd_destroy(tebd_handle h) {
   if (h->Gblk) cudaFree(h->Gblk);
   for (void* p : h->allocs) cudaFree(p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->h_gw) cudaFreeHost(h->h_gw);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
   cudaGetLastError();
   delete h;
+}
+
+int tebd_graph_stats(tebd_handle h, long long* replays, long long* fallbacks, long long* launches_per_replay) {
+  CHECK_HANDLE(h);
+  if (replays) *replays = h->graph_replays;
+  if (fallbacks) *fallbacks = h->graph_fallbacks;
+  if (launches_per_replay) *launches_per_replay = h->gexec ? h->glaunches : 0;
+  return TEBD_OK;
 }
 
 }  // extern "C"

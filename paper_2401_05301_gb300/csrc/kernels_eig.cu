@@ -154,20 +154,20 @@ __device__ void gershgorin(const double* d, const double* e, int m, double* sh, 
   gu = -block_min(hi, sh);
 }
 
-// Multisection with 8 points: a warp serves four eigenvalues, eight lanes each; per
-// iteration the lanes of a group count the eigenvalues below 8 interior points of
-// their interval, which shrinks it 9-fold (~17 iterations to machine precision).
-// Measured on GB300 this balances the serial Sturm recurrences (latency) against
-// the FP64 work of the counts (32 points: 11 iterations but 4x the counts; plain
-// bisection: 52 iterations).
+// Multisection with 4 points: a warp serves eight eigenvalues, four lanes each; per
+// iteration the lanes of a group count the eigenvalues below 4 interior points of
+// their interval, which shrinks it 5-fold (~23 iterations to machine precision).
+// The counts are bound by the FP64 pipe once a batch holds many matrices (the
+// blocked form's charge blocks): 4 points take 92 counts per eigenvalue against
+// 136 with 8 points, at 1.35x the serial iterations.
 __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   const EigMat& M = b.a[blockIdx.y];
   const int m = M.m;
   __shared__ double sh[33];
   double gl, gu;
   gershgorin(M.d, M.e, m, sh, gl, gu);
-  const int lane = threadIdx.x & 31, g = lane >> 3, sub = lane & 7;
-  const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4 + g;
+  const int lane = threadIdx.x & 31, g = lane >> 2, sub = lane & 3;
+  const int j = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 8 + g;
   const bool active = j < M.kmax && j < m;
   const double bnorm = fmax(fabs(gl), fabs(gu));
   const double eps = DBL_EPSILON, tiny = DBL_MIN * fmax(1.0, bnorm * bnorm);
@@ -175,18 +175,18 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
   double hi = gu + 2.0 * eps * bnorm * m + 4.0 * tiny;
   const double atol = 2.0 * eps * bnorm + 4.0 * tiny;
   const int target = m - 1 - j;  // ascending index of the j-th largest
-  for (int it = 0; it < 40; ++it) {
+  for (int it = 0; it < 64; ++it) {
     const bool conv = !(hi - lo > atol);
     if (__all_sync(0xffffffffu, conv || !active)) break;
-    const double x = lo + (hi - lo) * (double)(sub + 1) * (1.0 / 9.0);
+    const double x = lo + (hi - lo) * (double)(sub + 1) * 0.2;
     const bool above = active && !conv && sturm_count(M.d, M.work, m, x) > target;  // eigenvalue below x
-    const unsigned gb = (__ballot_sync(0xffffffffu, above) >> (8 * g)) & 0xFFu;
-    const int l0 = gb ? (__ffs(gb) - 1) : 8;  // first point above the eigenvalue (8: none)
-    const double xa = __shfl_sync(0xffffffffu, x, 8 * g + (l0 > 0 ? l0 - 1 : 0));
-    const double xb = __shfl_sync(0xffffffffu, x, 8 * g + (l0 < 8 ? l0 : 7));
+    const unsigned gb = (__ballot_sync(0xffffffffu, above) >> (4 * g)) & 0xFu;
+    const int l0 = gb ? (__ffs(gb) - 1) : 4;  // first point above the eigenvalue (4: none)
+    const double xa = __shfl_sync(0xffffffffu, x, 4 * g + (l0 > 0 ? l0 - 1 : 0));
+    const double xb = __shfl_sync(0xffffffffu, x, 4 * g + (l0 < 4 ? l0 : 3));
     if (active && !conv) {
       if (l0 > 0) lo = xa;
-      if (l0 < 8) hi = xb;
+      if (l0 < 4) hi = xb;
     }
   }
   if (active && sub == 0) M.evals[j] = 0.5 * (lo + hi);
@@ -199,7 +199,10 @@ __global__ void k_bisect(const __grid_constant__ EigBatch b) {
 // floor_rel x the cut's trace).  One block per cut finds that threshold by
 // multisection on the summed Sturm counts: P points per matrix per iteration, each
 // iteration shrinking the bracket by P + 1, then writes per matrix the number of
-// its eigenvalues at or above the bracket's lower end (capped by kmax).
+// its eigenvalues at or above the bracket's lower end (capped by kmax).  The search
+// ends early at a point whose count is exactly the target.  A cut's counts all run on
+// one SM, whose FP64 pipe bounds them (every count is m dependent steps), so few
+// points per iteration (P <= 7) do less work in total than a wide multisection.
 __device__ __forceinline__ int count_at_or_above(const EigMat& M, double x) { return M.m - sturm_count(M.d, M.work, M.m, x); }
 
 __global__ void __launch_bounds__(1024) k_cut_counts(const ThrCut* __restrict__ cuts) {
@@ -238,8 +241,8 @@ __global__ void __launch_bounds__(1024) k_cut_counts(const ThrCut* __restrict__ 
     go_sh = cnt[0] > C.target;
   }
   __syncthreads();
-  const int P = max(1, min(63, (int)blockDim.x / max(C.n, 1)));
-  for (int it = 0; it < 40 && go_sh; ++it) {
+  const int P = max(1, min(7, (int)blockDim.x / max(C.n, 1)));
+  for (int it = 0; it < 80 && go_sh; ++it) {
     const double lo = lo_sh, hi = hi_sh;
     if (threadIdx.x < P) cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(1024) k_cut_counts(const ThrCut* __restrict__ 
       const double nhi = (jb + 1 < P) ? lo + (hi - lo) * (double)(jb + 2) / (double)(P + 1) : hi;
       lo_sh = nlo;
       hi_sh = nhi;
-      go_sh = (nhi - nlo) > 4.0 * DBL_EPSILON * fmax(fabs(nhi), DBL_MIN);
+      go_sh = (jb < 0 || cnt[jb] != C.target) && (nhi - nlo) > 4.0 * DBL_EPSILON * fmax(fabs(nhi), DBL_MIN);
     }
     __syncthreads();
   }
@@ -1142,14 +1145,14 @@ int eig_trace(const EigBatch& b, cudaStream_t s) {
 int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* status, cudaStream_t s) {
   if (b.n == 0) return 0;
   const int mm = max_m(b);
-  static int grid = 0;
-  if (grid == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
+  static int sms = 0, per_sm = 0;
+  if (sms == 0) {
+    int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_panel, TD_THREADS, 0);
-    grid = std::max(1, sms * std::min(per_sm, 3));
   }
+  const int grid = std::max(1, sms * std::min(per_sm, b.panel_blocks > 0 ? b.panel_blocks : 3));
   int launches = 0;
   int kend = 0;  // panels run while any matrix has columns before its tail
   for (int i = 0; i < b.n; ++i) kend = std::max(kend, tail_start(b.a[i].m));
@@ -1236,7 +1239,7 @@ int eig_bisect(const EigBatch& b, cudaStream_t s) {
   int km = 0;
   for (int i = 0; i < b.n; ++i) km = std::max(km, std::min(b.a[i].kmax, b.a[i].m));
   if (km == 0) return 0;
-  k_bisect<<<dim3((km + 15) / 16, b.n), 128, 0, s>>>(b);  // four warps, four eigenvalues each
+  k_bisect<<<dim3((km + 31) / 32, b.n), 128, 0, s>>>(b);  // four warps, eight eigenvalues each
   return 1;
 }
 

@@ -378,6 +378,51 @@ int launch_trace_product(const double2* X, const double2* Yt, int chi, double2* 
   return 1;
 }
 
+__global__ void k_graph_check_eig(const __grid_constant__ GraphEig g) {
+  const int t = threadIdx.x;
+  if (t == 0 && *g.bar_err != 0u) atomicOr(g.flag, 4);
+  if (t >= g.n) return;
+  const double tr = *g.trace[t];
+  if (!(isfinite(tr) && tr > 0.0)) {
+    atomicOr(g.flag, 1);
+    return;
+  }
+  const double floor_v = g.floor_rel[t] * tr;
+  if (!(g.evals[t][g.kmax[t] - 1] > floor_v)) atomicOr(g.flag, 2);
+}
+
+__global__ void k_graph_check_trunc(const __grid_constant__ GraphTrunc g) {
+  const int t = threadIdx.x;
+  if (t == 0 && *g.status != 0) atomicOr(g.flag, 16);
+  if (t >= g.n) return;
+  if (*g.chi[t] != g.expect[t]) atomicOr(g.flag, 8);
+  *g.w_out[t] = *g.w[t];
+}
+
+__global__ void k_scale_inv(double2* X, long long n, const double* norm) {
+  const double f = 1.0 / *norm;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double2 x = X[e];
+    X[e] = make_double2(x.x * f, x.y * f);
+  }
+}
+
+int launch_graph_check_eig(const GraphEig& g, cudaStream_t s) {
+  k_graph_check_eig<<<1, 32, 0, s>>>(g);
+  return 1;
+}
+
+int launch_graph_check_trunc(const GraphTrunc& g, cudaStream_t s) {
+  k_graph_check_trunc<<<1, 32, 0, s>>>(g);
+  return 1;
+}
+
+int launch_scale_inv(double2* X, long long n, const double* norm, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_scale_inv<<<grid_for(n), 256, 0, s>>>(X, n, norm);
+  return 1;
+}
+
 int launch_check_finite(const double* x, int n, int* status, cudaStream_t s) {
   k_check_finite<<<grid_for(n), 256, 0, s>>>(x, n, status);
   return 1;

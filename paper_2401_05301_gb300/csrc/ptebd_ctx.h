@@ -34,6 +34,7 @@ struct Triple {
   int m1, n1, K1, chi1, m2, n2, K2, chi2;
   double norm1, norm2, w1, w2;
   long long call;  // randomized truncation: index of cut 1's test matrix (cut 2: call + 1)
+  size_t gw1, gw2;  // graph capture: where the two cuts' discarded weights are recorded
 };
 
 struct U1Work;  // workspace of the blocked form (u1.cu)
@@ -52,6 +53,7 @@ struct tebd_ctx {
   int order = 2;  // Trotter order: 2 or 4 (gate table and layer schedule follow it)
   int jacobi_sweeps = 60;  // sweep limit of the host gate builder's Jacobi eigen-solver
   long long wait_clocks = 2000000000LL;  // limit of each grid-barrier wait in the reduction (~1 s)
+  int panel_blocks = 0;  // blocks per SM of the reduction's cooperative grid (0 = automatic)
   cudaStream_t stream = nullptr;
   int device = 0;
   int sticky = TEBD_OK;
@@ -98,6 +100,30 @@ struct tebd_ctx {
   long long prof_launches[TEBD_PROF_NCLASS] = {};
   double prof_work[TEBD_PROF_NCLASS] = {};
   std::vector<cudaEvent_t> event_pool;
+  // CUDA-graph replay of whole steps (option "graph", dense three-site form, every bond
+  // at capacity): while a step is captured, every decision the host would read back
+  // (eigenvector count, chi', norms, status) is fixed to its saturated value and
+  // checked on the device instead; a replay whose checks fail is undone from the
+  // backup the graph takes first, and the step is run again the ordinary way.
+  bool graph = false;
+  bool capturing = false;       // the driving handle is being captured
+  long long generation = 0;     // bumped by every host change of the state or options
+  int* d_gflag = nullptr;       // device: failed checks of the replay (0 = accepted)
+  double* d_gw = nullptr;       // device: discarded weights of the captured truncations
+  size_t gw_cap = 0, gw_n = 0;
+  double* h_gw = nullptr;       // pinned copy of [flag, weights]
+  std::vector<std::pair<tebd_ctx*, std::pair<size_t, size_t>>> gw_map;  // (handle, w1, w2 index) per update
+  std::vector<std::pair<tebd_ctx*, int>> gcount;  // gate updates per handle per replay
+  std::vector<tebd_ctx*> gkey;   // the handles the cached graph steps
+  std::vector<long long> ggen;   // their generations at capture
+  cudaGraphExec_t gexec = nullptr;
+  long long glaunches = 0;       // kernel launches in one replay
+  double2* bkB = nullptr;        // backup of the state (B_k then lambda_k, packed by capacity)
+  size_t bk_bytes = 0;
+  long long graph_replays = 0, graph_fallbacks = 0;
+  cudaStream_t own_stream = nullptr;  // created for graph mode when the handle had the legacy stream
+  bool graph_broken = false;  // a capture failed: no graph for this handle until "graph" is set again
+  int graph_test_fallback = 0;  // diagnostic: undo this many accepted replays as if a check had failed
 };
 
 namespace ptebd {

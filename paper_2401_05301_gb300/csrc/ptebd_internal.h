@@ -188,6 +188,7 @@ struct EigBatch {
   int n;
   unsigned int* bar;  // grid-barrier state {count, generation, error} for the persistent reduction
   long long wait_clocks;  // limit of each grid-barrier wait of the reduction (clock64 ticks)
+  int panel_blocks;       // blocks per SM of the reduction's cooperative grid (0: as many as fit, at most 3)
 };
 
 constexpr int EIG_PARTS = 384;  // partial sums of p^+ v, one per strip of 32 columns (m <= 12288)
@@ -287,5 +288,35 @@ int launch_pair_hop(const double2* B, const double* lam, int chl, int d, int chr
 int launch_trace_product(const double2* X, const double2* Yt, int chi, double2* out, cudaStream_t s);
 
 int launch_check_finite(const double* x, int n, int* status, cudaStream_t s);
+
+// ---- device-side checks of a captured step (CUDA-graph replay, api.cu) ------------------
+constexpr int GRAPH_MAXT = 32;
+// After the eigenvalues of a batch: each trace finite and positive, the kmax-th
+// eigenvalue above floor_rel x trace (so the host would have asked for all kmax
+// vectors), and no grid-barrier timeout.  Failed checks are OR-ed into *flag.
+struct GraphEig {
+  const double* evals[GRAPH_MAXT];
+  const double* trace[GRAPH_MAXT];
+  int kmax[GRAPH_MAXT];
+  double floor_rel[GRAPH_MAXT];
+  int n;
+  const unsigned int* bar_err;
+  int* flag;
+};
+int launch_graph_check_eig(const GraphEig& g, cudaStream_t s);
+// After a truncation: chi' equal to the capacity the capture assumed, the truncation
+// status clear; the discarded weight copied to w_out[i].
+struct GraphTrunc {
+  const int* chi[GRAPH_MAXT];
+  int expect[GRAPH_MAXT];
+  const double* w[GRAPH_MAXT];
+  double* w_out[GRAPH_MAXT];
+  int n;
+  const int* status;
+  int* flag;
+};
+int launch_graph_check_trunc(const GraphTrunc& g, cudaStream_t s);
+// X[0..n) *= 1 / *norm (the renormalisation of a rebuilt site, norm on the device)
+int launch_scale_inv(double2* X, long long n, const double* norm, cudaStream_t s);
 
 }  // namespace ptebd

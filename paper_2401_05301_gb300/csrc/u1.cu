@@ -931,6 +931,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
       EigBatch eb{};
       eb.bar = c->d_bar;
       eb.wait_clocks = c->wait_clocks;
+      eb.panel_blocks = c->panel_blocks;
       for (size_t j = g0; j < std::min(jobs.size(), g0 + EIG_MAXP); ++j) eb.a[eb.n++] = mat(jobs[j]);
       c->launches += eig_trace(eb, c->stream);
       const int nl = eig_tridiagonalize(eb, mixed, ozw, c->d_status, c->stream);
@@ -1107,6 +1108,7 @@ int decompose(tebd_ctx* c, std::vector<Cut*>& cuts, std::vector<char*>& bases, s
       EigBatch eb{};
       eb.bar = c->d_bar;
       eb.wait_clocks = c->wait_clocks;
+      eb.panel_blocks = c->panel_blocks;
       for (size_t j = g0; j < std::min(vj.size(), g0 + EIG_MAXP); ++j) eb.a[eb.n++] = mat(vj[j]);
       c->launches += eig_vectors(eb, mixed, ozw, c->d_status, c->stream);
     }
