@@ -475,8 +475,14 @@ __global__ void __launch_bounds__(NT) k_backtransform(const __grid_constant__ Ei
 // U^T <- U^T - V T (V^+ U^T), i.e. three matrix products per block on the rows of U.
 constexpr int BT = 64;  // reflectors per block
 
+// Trailing indices per slab of the reduction's Hermitian product.  A function of the matrix's
+// own size, so its arithmetic could never depend on its batch; measured on GB300, 64-wide
+// slabs for the blocked form's sizes (more items per column, more partial sums per strip)
+// were slower than 256 at every size, so every matrix takes 256.
+__host__ __device__ __forceinline__ int td_chunk(int) { return 256; }
+
 __host__ __device__ inline size_t bt_offset(int m) {
-  const size_t slabs = (size_t)((m + 31) / 32) * ((m + 255) / 256);
+  const size_t slabs = (size_t)((m + 31) / 32) * ((m + td_chunk(m) - 1) / td_chunk(m));
   return (size_t)m * 128 + (size_t)EIG_PARTS * 64 + slabs * 64;
 }
 // V (m x BT) and conj(V) reuse the panel arrays; then G = V^+ V, T^T, S = U conj(V), S T^T.
@@ -552,7 +558,6 @@ constexpr int TD_THREADS = 256;
 constexpr int TD_WARPS = TD_THREADS / 32;
 constexpr int TD_STRIP = 32;
 constexpr int TD_NB = 32;      // columns per panel of the blocked reduction
-constexpr int TD_CHUNK = 256;  // trailing indices per slab of the Hermitian product
 // A column whose largest off-diagonal entry lies below 2^-900 is taken as already
 // reduced (tau = 0).  The Gram matrices here have trace ~1, so such entries are far
 // below their rounding; they do arise, as rounding noise that each Gram product
@@ -798,7 +803,7 @@ __device__ void phase1_regs(const EigMat& M, int k, int j, double* sh, double2* 
 // w_i v_i^+) without forming A(k):
 //   phase 1 (a block per matrix): w of column k-1 and the last term of row k (see
 //           phase 3); the reflector of column k (v_k, tau_k).
-//   phase 2 (slabs of 32 x TD_CHUNK): h = A(k0) v over the stored upper triangle,
+//   phase 2 (slabs of 32 x td_chunk(m)): h = A(k0) v over the stored upper triangle,
 //           and per-strip partials of w_i^+ v and v_i^+ v.
 //   phase 3 (strips of 32): p = tau (h - sum_i (v_i (w_i^+ v) + w_i (v_i^+ v))), the
 //           strip partials of p^+ v for alpha, and row k+1 brought to A(k+1) except
@@ -816,6 +821,7 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
   __shared__ double2 rv_sh[TD_WARPS][TD_STRIP];
   __shared__ double red_sh[33];
   __shared__ double2 scale_sh;
+  __shared__ int pre2[EIG_MAXP + 1], pre3[EIG_MAXP + 1];  // items of phase 2 / 3 before each matrix
   unsigned int target = 0;  // barrier count expected at the next grid_sync
   for (int k = k0; k < k1; ++k) {
     const int j = k - k0;
@@ -851,25 +857,41 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
     }
     if (!grid_sync(b.bar, target, b.wait_clocks)) return;
     // ---- phase 2: h = A(k0) v by slabs.  Item (s, q) covers strip s (32 columns) and
-    // chunk q (TD_CHUNK indices) of the trailing set: the column part reads the stored
+    // chunk q (td_chunk(m) indices) of the trailing set: the column part reads the stored
     // rows r in chunk q above the strip's columns (r <= c, used as conj(A[r][c]) v[r]),
     // the row part reads the strip's rows at columns c > row in chunk q.  Every item
-    // holds about 32 x TD_CHUNK elements, so the work balances across blocks.
-    for (int item = blockIdx.x;; item += gridDim.x) {
-      int rem = item, mi = -1;
-      for (int i = 0; i < b.n; ++i) {
-        const int n = (k < tail_start(b.a[i].m)) ? b.a[i].m - k - 1 : 0;
-        const int ni = (n > 0) ? ((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK) : 0;
-        if (rem < ni) { mi = i; break; }
-        rem -= ni;
+    // holds about 32 x chunk elements, so the work balances across blocks.  The items
+    // before each matrix are counted once per column (pre2, pre3) and an item finds its
+    // matrix by binary search.
+    if (threadIdx.x < b.n) {  // items of each matrix, then their prefix sums
+      const int i = threadIdx.x;
+      const int n = (k < tail_start(b.a[i].m)) ? b.a[i].m - k - 1 : 0;
+      const int ch = td_chunk(b.a[i].m);
+      pre2[i + 1] = (n > 0) ? ((n + TD_STRIP - 1) / TD_STRIP) * ((n + ch - 1) / ch) : 0;
+      pre3[i + 1] = (n > 0) ? (n + TD_STRIP - 1) / TD_STRIP : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      pre2[0] = pre3[0] = 0;
+      for (int i = 1; i <= b.n; ++i) {
+        pre2[i] += pre2[i - 1];
+        pre3[i] += pre3[i - 1];
       }
-      if (mi < 0) break;
+    }
+    __syncthreads();
+    for (int item = blockIdx.x; item < pre2[b.n]; item += gridDim.x) {
+      int lo = 0, hi = b.n - 1;  // the last matrix whose first item is <= item
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre2[mid] <= item) lo = mid; else hi = mid - 1;
+      }
+      const int mi = lo, rem = item - pre2[mi];
       const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1;
-      const int nq = (n + TD_CHUNK - 1) / TD_CHUNK;
+      const int m = M.m, n = m - k - 1, ch = td_chunk(m);
+      const int nq = (n + ch - 1) / ch;
       const int sidx = rem / nq, q = rem % nq;
       const int c0 = sidx * TD_STRIP, w = min(TD_STRIP, n - c0);
-      const int q0 = q * TD_CHUNK, q1 = min(n, q0 + TD_CHUNK);
+      const int q0 = q * ch, q1 = min(n, q0 + ch);
       const double2* v = M.H + (size_t)k * m + k + 1;
       const double2* A = M.H + (size_t)(k + 1) * m + k + 1;
       const int c = c0 + lane;
@@ -926,19 +948,17 @@ __global__ void __launch_bounds__(TD_THREADS, 3) k_tridiag_panel(const __grid_co
     }
     if (!grid_sync(b.bar, target, b.wait_clocks)) return;
     // ---- phase 3: corrections, tau, the strip partials of p^+ v, and row k+1
-    for (int item = blockIdx.x;; item += gridDim.x) {
-      int rem = item, mi = -1;
-      for (int i = 0; i < b.n; ++i) {
-        const int n = (k < tail_start(b.a[i].m)) ? b.a[i].m - k - 1 : 0;
-        const int ns = (n > 0) ? (n + TD_STRIP - 1) / TD_STRIP : 0;
-        if (rem < ns) { mi = i; break; }
-        rem -= ns;
+    for (int item = blockIdx.x; item < pre3[b.n]; item += gridDim.x) {
+      int lo = 0, hi = b.n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre3[mid] <= item) lo = mid; else hi = mid - 1;
       }
-      if (mi < 0) break;
+      const int mi = lo, rem = item - pre3[mi];
       const EigMat& M = b.a[mi];
-      const int m = M.m, n = m - k - 1;
+      const int m = M.m, n = m - k - 1, ch = td_chunk(m);
       const int ns = (n + TD_STRIP - 1) / TD_STRIP;
-      const int nq = (n + TD_CHUNK - 1) / TD_CHUNK;
+      const int nq = (n + ch - 1) / ch;
       const int c0 = rem * TD_STRIP, w = min(TD_STRIP, n - c0);
       const double2* v = M.H + (size_t)k * m + k + 1;
       // Row k+1 (the next pivot, if it is in this panel) is brought to A(k+1) here,
@@ -1166,7 +1186,8 @@ int eig_tridiagonalize(const EigBatch& b, bool mixed, void* const* oz_ws, int* s
       if (k0 >= tail_start(b.a[i].m)) continue;
       ++active;
       const int n = b.a[i].m - k0 - 1;
-      if (n > 0) items += (long long)((n + TD_STRIP - 1) / TD_STRIP) * ((n + TD_CHUNK - 1) / TD_CHUNK);
+      const int ch = td_chunk(b.a[i].m);
+      if (n > 0) items += (long long)((n + TD_STRIP - 1) / TD_STRIP) * ((n + ch - 1) / ch);
     }
     const int gsz = (int)std::min<long long>(grid, std::max<long long>(active, items));
     cudaMemsetAsync(b.bar, 0, sizeof(unsigned int), s);  // arrival count of the grid barrier
@@ -1226,7 +1247,7 @@ size_t eig_panel_doubles2(int m) {
   // panel arrays, then the back-transformation's G, T^T, S and S T^T
   return bt_offset(m) + 2 * BT * BT + (size_t)2 * m * BT;
 }
-static_assert(BT == 2 * TD_NB && TD_STRIP == 32 && TD_CHUNK == 256, "bt_offset() mirrors the panel layout");
+static_assert(BT == 2 * TD_NB && TD_STRIP == 32, "bt_offset() mirrors the panel layout");
 
 int eig_cut_counts(const ThrCut* cuts_dev, int ncuts, cudaStream_t s) {
   if (ncuts <= 0) return 0;
