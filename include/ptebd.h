@@ -181,10 +181,11 @@ int tebd_step(tebd_handle h, int n_steps);
 int tebd_estimate_bytes(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 
 /* tebd_estimate_bytes for a handle of the particle-number-blocked form (option
- * "u1"): dense site tensors, gates and their occupation blocks, and per workspace
- * slot an arena allowance for a saturated local update (the blocked arenas grow
- * with the charge blocks; the allowance is a fixed fraction of the dense theta,
- * 16 chi_max^2 d^3 bytes, calibrated on a saturated chi = 1024, d = 5 state).
+ * "u1"): dense site tensors, gates and their occupation blocks, per workspace slot
+ * an arena allowance for a saturated local update, and the exact-digit workspace
+ * rings (the blocked arenas grow with the charge blocks; both allowances are fixed
+ * multiples of the dense theta, 16 chi_max^2 d^3 bytes, fitted to the measured
+ * footprint of a saturated chi = 1024, d = 5 state with 4, 8 and 21 slots).
  * Host-only arithmetic.  Serving infrastructure (no counterpart in the paper). */
 int tebd_estimate_bytes_u1(int L, int n_max, int chi_max, int max_slots, int precision, double* bytes);
 

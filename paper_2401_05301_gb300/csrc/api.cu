@@ -85,12 +85,16 @@ int ensure_pinned(tebd_ctx* c, size_t n) {
 
 namespace {
 
-// Arena bytes of one blocked local update at saturation, as a fraction of the dense
-// theta (16 chi^2 d^3): the blocked arenas hold the compact theta and C (each at most
-// max_Delta n_Delta / d^3 of the dense one), the packed blocks of both cuts and their
-// eigen-solver buffers; measured at the chi = 1024, d = 5 headline state (see the
-// bench's device_bytes) and rounded up.
-constexpr double U1_ARENA_FRACTION = 0.5;
+// Device bytes of the blocked form beyond the state, as multiples of the dense theta
+// (16 chi^2 d^3): per workspace slot the arenas of one saturated local update (the compact
+// theta and C, the packed blocks of both cuts and their eigen-solver buffers), and once
+// per handle the exact-digit workspace rings (16 products, 64 eigen-solver matrices, each
+// sized for the largest block).  Fitted to tebd_device_bytes of the saturated chi = 1024,
+// d = 5, L = 64 state after four steps: 19.7 / 25.2 / 37.9 GB with 4 / 8 / 21 slots (the
+// per-slot high-water mark is largest with few slots, each of which sees several triples),
+// so the estimate is exact at 4 and 8 slots and 14 % high at 21.
+constexpr double U1_ARENA_FRACTION = 0.655;
+constexpr double U1_RING_FRACTION = 4.5;
 
 int max_triples_per_layer(int L, bool ss = false) {
   const int stride = ss ? 2 : 3, span = ss ? 1 : 2;  // super sites: NN bonds, two layers
@@ -1535,7 +1539,8 @@ int tebd_estimate_bytes_u1(int L, int n_max, int chi_max, int max_slots, int pre
   int slots = std::min(max_triples_per_layer(L), MAX_SLOTS);
   if (max_slots > 0) slots = std::min(slots, max_slots);
   b += slots * U1_ARENA_FRACTION * 16.0 * (double)capmax * capmax * D;
-  b += 40.0 * L + 64.0e6;  // measurement buffers, staging, exact-digit ring
+  b += U1_RING_FRACTION * 16.0 * (double)capmax * capmax * D;  // exact-digit workspace rings
+  b += 40.0 * L + 64.0e6;  // measurement buffers, staging
   *bytes = b;
   return TEBD_OK;
 }
