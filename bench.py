@@ -1,6 +1,6 @@
 """Benchmark: TEBD gate-updates/s at chi_max on one GB300 (and N replicas).
 
-Workload (default, "config3_u1"): the mixed-precision chain of L = 64 sites,
+Workload (default, "L64_d5_chi1024_u1"): the mixed-precision chain of L = 64 sites,
 n_max = 4 (d = 5), U = 3, J = 1, J_NNN = 0.1, K = 0.003 about j_c = 32.5,
 dt = 0.005, chi_max = 1024, relative cut eps = 1e-12, at half filling
 (N = 32), started from the seeded charge-labelled synthetic saturated state
@@ -236,7 +236,7 @@ def time_path(precision: int, state, stream, steps: int, warmup: int, ws: int, b
     return out
 
 
-def dense_config2(stream, steps: int = 2, warmup: int = 1):
+def dense_L32(stream, steps: int = 2, warmup: int = 1):
     """The dense form on the L = 32, d = 4, chi = 256 chain (w_cut = 1e-10) from its seeded
     synthetic saturated state: mixed, plain FP64 and exact-digit paths."""
     import torch
@@ -271,15 +271,15 @@ def dense_config2(stream, steps: int = 2, warmup: int = 1):
     return out
 
 
-SERVE_REQUESTS = 16      # config 5 streams 500; scaled to fit a bounded run
-SERVE_STEPS = (12, 6)    # steps of the headline-style / large requests (config 5: to t = 8 / t = 6)
+SERVE_REQUESTS = 16      # the served mix is 500 requests; scaled to fit a bounded run
+SERVE_STEPS = (12, 6)    # steps of the headline-style / large requests (unscaled: to t = 8 / t = 6)
 SERVE_SLOTS = 4          # workspace slots per request (more requests fit the budget)
 SERVE_CONCURRENT = 6     # the HBM budget admits about this many headline-style requests at once
 
 
 def serve_stream(rate: float, seed: int = workloads.SEED, n: int = SERVE_REQUESTS, blocked: bool = True,
                  at_once: bool = False):
-    """Config 5's request mix, scaled: 90% chains like the headline (L=64, d=5, chi_max=1024, U=3,
+    """The served request mix, scaled: 90% chains like the headline (L=64, d=5, chi_max=1024, U=3,
     J_NNN=0.1, K=0.003 about j_c=32.5, dt=0.005) and 10% large jobs (L=100, d=4, chi_max=2048, U=5,
     J_NNN=0.1, K=0.002 about j_c=50.5, dt=0.01), each from its CDW state, measured every 4 steps.
     Seeded draws: the exponential inter-arrival times first, then the request types."""
@@ -329,8 +329,8 @@ def served_measurement(stream_ptr):
         loads[f"{load:g}"] = st
     fifo_stats, fifo_s, _ = serve(serve_stream(0.9 * capacity, blocked=False), precision=0, max_active=1,
                                   hbm=float("inf"))
-    return {"workload": (f"config 5's mix scaled: {SERVE_REQUESTS} Poisson requests (500 in config 5), 90% "
-                         f"L=64 d=5 chi_max=1024 for {SERVE_STEPS[0]} steps (t=8 in config 5), 10% L=100 d=4 "
+    return {"workload": (f"served mix scaled: {SERVE_REQUESTS} Poisson requests (500 unscaled), 90% "
+                         f"L=64 d=5 chi_max=1024 for {SERVE_STEPS[0]} steps (t=8 unscaled), 10% L=100 d=4 "
                          f"chi_max=2048 for {SERVE_STEPS[1]} steps (t=6), each from its CDW state, "
                          f"{SERVE_SLOTS} workspace slots per request"),
             "hbm_budget_bytes": budget, "footprint_bytes": {"headline_style": small, "large": large},
@@ -340,7 +340,7 @@ def served_measurement(stream_ptr):
 
 
 def batched_measurement(stream_ptr, steps: int = 1):
-    """Config 4: the 48 seeded simulations (L in 16..64, chi_max in 64..512, d = 4, seeded U, J_NNN,
+    """The 48-simulation batch: seeded simulations (L in 16..64, chi_max in 64..512, d = 4, seeded U, J_NNN,
     K; j_c = (L+1)/2), warm-started at chi_max: each from the charge-labelled synthetic saturated
     state of its chain at half filling (N = L/2), blocked form, mixed precision.  One
     `tebd_batch_step` over all 48 (every stage of a layer is one grouped launch over the triples of
@@ -396,7 +396,7 @@ def batched_measurement(stream_ptr, steps: int = 1):
 
 def graph_measurement(stream_ptr, steps: int = 6):
     """Launch-bound dense steps with and without CUDA-graph replay (option "graph"): the
-    first 16 of the config-4 simulations (L 16..64, d = 4) at chi_max capped to 64, each from
+    first 16 of the 48-simulation batch's draws (L 16..64, d = 4) at chi_max capped to 64, each from
     its dense synthetic saturated state, mixed precision, one batch.  Both arms run two untimed
     steps first (with the option on: one ordinary, one captured), then `steps` timed steps."""
     import torch
@@ -431,7 +431,7 @@ def graph_measurement(stream_ptr, steps: int = 6):
 
     plain = arm(False)
     graph = arm(True)
-    return {"workload": f"16 seeded simulations (config-4 draws, L 16..64, d=4, chi_max capped at 64) from dense "
+    return {"workload": f"16 seeded simulations (the 48-batch's first draws, L 16..64, d=4, chi_max capped at 64) from dense "
                         f"synthetic saturated states, one batch, mixed precision, {steps} steps after two untimed",
             "unit": UNIT, "ordinary": plain, "graph": graph, "speedup": graph["value"] / plain["value"]}
 
@@ -472,7 +472,7 @@ def run_dense_workload(args):
     """--workload trunc_L32: the dense form on the L = 32, d = 4, chi = 256 chain alone."""
     import torch
     torch.cuda.set_device(0)
-    out = dense_config2(torch.cuda.current_stream(), steps=args.steps, warmup=args.warmup)
+    out = dense_L32(torch.cuda.current_stream(), steps=args.steps, warmup=args.warmup)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -483,8 +483,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config3_u1", choices=["config3_u1", "u1_L24", "trunc_L32"],
-                    help="config3_u1: the headline (L=64 d=5 chi=1024, blocked form); u1_L24: the same physics and "
+    ap.add_argument("--workload", default="L64_d5_chi1024_u1", choices=["L64_d5_chi1024_u1", "u1_L24", "trunc_L32"],
+                    help="L64_d5_chi1024_u1: the headline (L=64 d=5 chi=1024, blocked form); u1_L24: the same physics and "
                          "local sizes on 24 sites (N=12; a small case for profiling); trunc_L32: the dense form alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true", help="skip the served p50/p99 measurement")
@@ -605,7 +605,7 @@ def main():
         bound, peak, src = "tensor", tf32_peak, ("measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)" if bf16
                                                  else "fallback 1.9 PFLOP/s bf16 x 1.1/2.25")
     traffic, tnote = None, None
-    if dom == "tridiag" and args.workload == "config3_u1":
+    if dom == "tridiag" and args.workload == "L64_d5_chi1024_u1":
         # dram__bytes_read.sum + dram__bytes_write.sum of one k_tridiag_panel launch (the step's first
         # panel, up to 64 charge blocks) from the ncu capture summarised in
         # profiles/k_tridiag_panel_u1_L24_d5_chi1024.md; the same kernel and local sizes as this chain
@@ -632,9 +632,9 @@ def main():
     batched = None
     if not args.no_batched and ws == 1:
         batched = side_measurement(batched_measurement, stream.cuda_stream)
-    config2 = None
+    dense32 = None
     if not args.no_side and ws == 1:
-        config2 = side_measurement(dense_config2, stream)
+        dense32 = side_measurement(dense_L32, stream)
     graphm = None
     if not args.no_graph and ws == 1:
         graphm = side_measurement(graph_measurement, stream.cuda_stream)
@@ -666,7 +666,7 @@ def main():
             "mixed_over_fp64": ((fp64["ms_per_step"] / (ms_side / side)) if isinstance(fp64, dict) and
                                 fp64.get("ms_per_step") else None),
             "mixed_ms_per_step_side_steps": ms_side / side,
-            "dense_config2": config2, "served": served, "batched": batched, "graph": graphm}
+            "dense_L32_d4_chi256": dense32, "served": served, "batched": batched, "graph": graphm}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
