@@ -122,3 +122,40 @@ def test_charge_labelled_synthetic_state():
             assert len(u.lam[b]) == len(o.lam[b])
             assert np.max(np.abs(u.lam[b] - o.lam[b])) < 1e-12
     assert u.block_fraction() < 0.1
+
+
+def test_mutation_per_block_truncation_is_caught(monkeypatch):
+    """A planted reading mistake: rule T applied to each charge block on its own (with the block's
+    own weight as the total) instead of once to the merged spectrum of the cut.  On the truncating
+    L = 32 chain the blocked chi' then leaves the dense oracle's, which the pin above requires."""
+    from oracle import u1 as u1mod
+
+    def per_block(self, M, row_q, col_q):
+        keep_s, keep_v, keep_q = [], [], []
+        w_all = 0.0
+        for c in np.unique(row_q):
+            r, k = np.flatnonzero(row_q == c), np.flatnonzero(col_q == c)
+            if len(k) == 0:
+                continue
+            _, s, Vh = u1mod.svd_desc(M[np.ix_(r, k)])
+            if not np.sum(s * s) > 0.0:
+                continue
+            n, w = u1mod.truncation_rule(s, self.chi_max, self.w_cut, self.eps_rel)
+            w_all += w
+            for j in range(n):
+                row = np.zeros(M.shape[1], dtype=M.dtype)
+                row[k] = Vh[j]
+                keep_s.append(s[j]), keep_v.append(row), keep_q.append(c)
+        order = np.argsort(-np.array(keep_s), kind="stable")[: self.chi_max]
+        s = np.array(keep_s)[order]
+        norm = np.sqrt(np.sum(s * s))
+        return s / norm, np.array(keep_v)[order], np.array(keep_q)[order], norm, w_all
+
+    monkeypatch.setattr(U1TEBD, "_block_svd", per_block)
+    wl = workloads.TRUNC_L32
+    u, o = U1TEBD(**_args(wl)), TEBD(**_args(wl))
+    u.init_product(wl.occupation())
+    o.init_product(wl.occupation())
+    u.step(10)
+    o.step(10)
+    assert u.chi() != o.chi()
