@@ -119,3 +119,34 @@ def test_test_matrices_are_an_input():
         RandomizedTEBD(6, 2, 16, 1.0, 1.0, 0.1, 0.0, 3.5, 0.01)
     a, b = _omega(10, 4, 3), _omega(10, 4, 3)
     assert np.array_equal(a, b) and not np.array_equal(a, _omega(10, 4, 4))
+
+
+def test_mutation_tail_from_the_sketch_is_caught(monkeypatch):
+    """A planted mistake: rule T's total taken from the sketched values (sum of s^2 over the l
+    computed values) instead of ||theta'||_F^2.  With a sketch of exactly chi_max = 16 columns the
+    discarded weight then reads zero, far outside the 1e-3 of the dense oracle's that the pin above
+    allows (the correct total gives the exact tail for any sketch size)."""
+    from oracle import randomized as rmod
+
+    def bad(self, M):
+        m, n = M.shape
+        l = min(self.chi_max + self.oversample, m, n)
+        omega = self.omega_fn(n, l, self.calls)
+        self.calls += 1
+        _, s, Vh = rmod.randomized_svd(M, omega, self.power_iters)
+        total = float(np.sum(s * s))
+        k, w = rmod.truncation_rule_partial(s, total, self.chi_max, self.w_cut, self.eps_rel)
+        s = s[:k]
+        norm = np.sqrt(np.sum(s * s))
+        return s / norm, Vh[:k], norm, w
+
+    monkeypatch.setattr(RandomizedTEBD, "_truncated_svd", bad)
+    wl = workloads.PARITY_L8
+    args = (wl.L, wl.n_max, 16, wl.U, wl.J, wl.Jnnn, wl.K, wl.jc, wl.dt)
+    r = RandomizedTEBD(*args, w_cut=0.0, eps_rel=1e-12, omega_fn=_omega, oversample=0, power_iters=2)
+    o = TEBD(*args, w_cut=0.0, eps_rel=1e-12)
+    r.init_product(wl.occupation())
+    o.init_product(wl.occupation())
+    r.step(100)
+    o.step(100)
+    assert abs(r.w_total - o.w_total) > 1e-3 * o.w_total
